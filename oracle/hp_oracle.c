@@ -1,0 +1,564 @@
+/*
+ * hp_oracle.c -- plain, slow CPU definition of the single-pulse search hot
+ * path of Heimdall++ (arXiv 2512.00398), used ONLY as test infrastructure.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg (and
+ * its --impl reference arm) may load this code.  The CUDA library never links,
+ * includes or calls it, and it shares no code with the library.
+ *
+ * Every step follows the pipeline of Section II-B (stage list) and Algorithm 1
+ * (per-trial loop: baseline removal, normalisation, matched filtering, peak
+ * detection; then merging/clustering).  The paper names the stages but prints
+ * no formulas except the DM integral (Eq. 1); the readings used where it is
+ * silent are listed next to each function and in the design doc.
+ *
+ * Arithmetic: exact integers (int64) for every sum; FP64 for sigma, the
+ * threshold and S/N.  Build with -ffp-contract=off so that no multiply-add
+ * is fused (the decisions S >= thr*sigma*sqrt(W) must be reproducible).
+ *
+ * Parity status per function (pins live in tests/test_oracle_*.py):
+ *   hpo_delays            pinned: closed form, hand-worked values, invariants
+ *   hpo_dedisperse_rows   pinned: impulse response, DM-0 channel sum, brute force
+ *   hpo_remedian/baseline pinned: ramp reproduction, constant, spike rejection,
+ *                                 brute-force recursion, monotone-input median
+ *   hpo_baseline_mean     pinned: brute-force window mean
+ *   hpo_mad               pinned: numpy sort median, Gaussian unit RMS
+ *   hpo_detect_trial      pinned: naive window sums, rectangular pulse, brute-force runs
+ *   hpo_merge             pinned: brute-force O(N^2) components, permutation invariance
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define HPO_OK 0
+#define HPO_ERR_ARG -1
+#define HPO_ERR_OVERFLOW -4
+#define HPO_ERR_SHORT -6
+
+/* Cold-plasma dispersion constant, s MHz^2 pc^-1 cm^3. */
+static const double HPO_KDM = 4148.808;
+/* Consistency factor of the median absolute deviation for Gaussian noise,
+ * 1 / Phi^-1(3/4). */
+static const double HPO_MAD_TO_SIGMA = 1.482602218505602;
+
+int hpo_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------
+ * Step c1: per-channel, per-trial delay in samples (Section II-B, Eq. 1 and
+ * the cold-plasma law).  Channel c is at f_c = f_top + c*chan_bw MHz, the
+ * reference frequency is f_top (so channel 0 has zero delay), and the delay
+ * in seconds K*DM*(f_c^-2 - f_top^-2) is divided by tsamp and rounded to the
+ * nearest integer, halves to even (rint).
+ * ---------------------------------------------------------------------- */
+int hpo_delays(int nchans, double f_top, double chan_bw, double tsamp,
+               const float* dm_list, int ndm, int32_t* out /* [ndm][nchans] */) {
+    if (nchans <= 0 || ndm <= 0 || !(tsamp > 0.0) || !(f_top > 0.0)) return HPO_ERR_ARG;
+    double inv_top2 = 1.0 / (f_top * f_top);
+    for (int d = 0; d < ndm; ++d) {
+        double dm = (double)dm_list[d];
+        for (int c = 0; c < nchans; ++c) {
+            double f = f_top + (double)c * chan_bw;
+            double sec = HPO_KDM * dm * (1.0 / (f * f) - inv_top2);
+            out[(int64_t)d * nchans + c] = (int32_t)rint(sec / tsamp);
+        }
+    }
+    return HPO_OK;
+}
+
+/* Largest delay of the table (the last usable input sample offset). */
+int32_t hpo_max_delay(const int32_t* delays, int ndm, int nchans) {
+    int32_t m = 0;
+    for (int64_t i = 0; i < (int64_t)ndm * nchans; ++i)
+        if (delays[i] > m) m = delays[i];
+    return m;
+}
+
+/* ------------------------------------------------------------------------
+ * Step c2: incoherent dedispersion (Section II-B): for every trial d and
+ * output sample t in [0, nout), D[d][t] = sum_c x[t + delay(c,d)][c].
+ * Only samples whose every term lies inside the input are produced
+ * (nout = nsamps - max delay).  Rows d_begin..d_end-1 are written to
+ * out[(d - d_begin)][t].  The sum is formed in int64 and must fit int32.
+ * ---------------------------------------------------------------------- */
+int hpo_dedisperse_rows(const uint8_t* x, int64_t nsamps, int nchans,
+                        const int32_t* delays, int d_begin, int d_end,
+                        int64_t nout, int32_t* out) {
+    if (nout < 0 || d_end < d_begin) return HPO_ERR_ARG;
+    int nrows = d_end - d_begin;
+    const int64_t TB = 4096;
+    int64_t ntb = (nout + TB - 1) / TB;
+    int bad = 0;
+#pragma omp parallel for collapse(2) schedule(dynamic) reduction(| : bad)
+    for (int r = 0; r < nrows; ++r) {
+        for (int64_t tb = 0; tb < ntb; ++tb) {
+            const int32_t* dl = delays + (int64_t)(d_begin + r) * nchans;
+            int64_t t1 = (tb + 1) * TB < nout ? (tb + 1) * TB : nout;
+            for (int64_t t = tb * TB; t < t1; ++t) {
+                int64_t acc = 0;
+                for (int c = 0; c < nchans; ++c) {
+                    int64_t row = t + dl[c];
+                    if (row < 0 || row >= nsamps) { bad = 1; continue; }
+                    acc += x[row * nchans + c];
+                }
+                if (acc > INT32_MAX) bad = 1;
+                out[(int64_t)r * nout + t] = (int32_t)acc;
+            }
+        }
+    }
+    return bad ? HPO_ERR_ARG : HPO_OK;
+}
+
+/* One dedispersed sample, for sampled checks of large runs. */
+int64_t hpo_dedisperse_point(const uint8_t* x, int nchans, const int32_t* delay_row, int64_t t) {
+    int64_t acc = 0;
+    for (int c = 0; c < nchans; ++c) acc += x[(t + delay_row[c]) * nchans + c];
+    return acc;
+}
+
+/* ------------------------------------------------------------------------
+ * Helpers: exact lower median of r <= 5 values, floor division.
+ * ---------------------------------------------------------------------- */
+static int64_t lower_median_small(const int64_t* v, int r) {
+    int64_t s[5];
+    for (int i = 0; i < r; ++i) s[i] = v[i];
+    for (int i = 1; i < r; ++i) {            /* insertion sort */
+        int64_t key = s[i];
+        int j = i - 1;
+        while (j >= 0 && s[j] > key) { s[j + 1] = s[j]; --j; }
+        s[j + 1] = key;
+    }
+    return s[(r - 1) / 2];
+}
+
+static int64_t floor_div(int64_t a, int64_t b) {     /* b > 0 */
+    int64_t q = a / b;
+    if ((a % b) != 0 && (a < 0)) --q;
+    return q;
+}
+
+/* Number of remedian levels for a window of `win` samples: the largest L with
+ * 5^L <= win (integer form of floor(log5(win))). */
+int hpo_remedian_levels(int64_t win) {
+    int L = 0;
+    int64_t p = 1;
+    while (win >= 1 && p <= win / 5) { p *= 5; ++L; }
+    return L;
+}
+
+/* ------------------------------------------------------------------------
+ * Step c3 (median mode): baseline removal by a running median (Section II-B,
+ * "Baseline Removal"; the paper only names a moving average, the running
+ * median is the robust reading).  The running median is the remedian of
+ * Rousseeuw & Bassett (1990): level 0 is the series, level l+1 holds the
+ * medians of consecutive groups of five level-l values, a trailing group of
+ * r < 5 values taking its lower median.  After L levels value m_j stands for
+ * input samples [5^L j, 5^L (j+1)) and is placed at the centre
+ * c_j = 5^L j + (5^L - 1)/2.
+ * Writes the level-L values to m (capacity >= ceil(n / 5^L)) and returns
+ * their count.
+ * ---------------------------------------------------------------------- */
+int64_t hpo_remedian(const int32_t* D, int64_t n, int L, int64_t* m) {
+    if (n <= 0) return 0;
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!cur) return -1;
+    for (int64_t i = 0; i < n; ++i) cur[i] = D[i];
+    int64_t cn = n;
+    for (int l = 0; l < L; ++l) {
+        int64_t nn = (cn + 4) / 5;
+        for (int64_t j = 0; j < nn; ++j) {
+            int64_t a = 5 * j;
+            int r = (int)((cn - a) < 5 ? (cn - a) : 5);
+            cur[j] = lower_median_small(cur + a, r);   /* j <= a: in place is safe */
+        }
+        cn = nn;
+    }
+    memcpy(m, cur, sizeof(int64_t) * (size_t)cn);
+    free(cur);
+    return cn;
+}
+
+/* Baseline b(t) from the level-L values: linear between neighbouring centres,
+ *   b(t) = m_j + floor((m_{j+1} - m_j) * (t - c_j) / 5^L)   for c_j <= t < c_{j+1},
+ * held at m_0 before the first centre and at m_{M-1} after the last. */
+int hpo_baseline_median(const int32_t* D, int64_t n, int L, int64_t* b) {
+    if (n <= 0) return HPO_OK;
+    int64_t P = 1;
+    for (int l = 0; l < L; ++l) P *= 5;
+    int64_t M = (n + P - 1) / P;
+    int64_t* m = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+    if (!m) return HPO_ERR_ARG;
+    int64_t got = hpo_remedian(D, n, L, m);
+    if (got != M) { free(m); return HPO_ERR_ARG; }
+    int64_t half = (P - 1) / 2;
+    int64_t c_first = half, c_last = P * (M - 1) + half;
+    for (int64_t t = 0; t < n; ++t) {
+        if (t <= c_first) { b[t] = m[0]; continue; }
+        if (t >= c_last) { b[t] = m[M - 1]; continue; }
+        int64_t j = (t - half) / P;                   /* c_j <= t < c_{j+1} */
+        int64_t cj = P * j + half;
+        b[t] = m[j] + floor_div((m[j + 1] - m[j]) * (t - cj), P);
+    }
+    free(m);
+    return HPO_OK;
+}
+
+/* Step c3 (mean mode): the paper's "moving average subtraction" taken
+ * literally: b(t) = floor( sum_{|i-t| <= H, 0 <= i < n} D[i] / count ). */
+int hpo_baseline_mean(const int32_t* D, int64_t n, int64_t H, int64_t* b) {
+    if (n <= 0) return HPO_OK;
+    int64_t* pre = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!pre) return HPO_ERR_ARG;
+    pre[0] = 0;
+    for (int64_t i = 0; i < n; ++i) pre[i + 1] = pre[i] + D[i];
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t lo = t - H < 0 ? 0 : t - H;
+        int64_t hi = t + H > n - 1 ? n - 1 : t + H;
+        b[t] = floor_div(pre[hi + 1] - pre[lo], hi - lo + 1);
+    }
+    free(pre);
+    return HPO_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Step c4: normalisation by a robust RMS (Section II-B, "Normalization").
+ * MAD = lower median of |y| (element (n-1)/2 of the sorted values, exact);
+ * sigma = 1.482602218505602 * MAD.
+ * ---------------------------------------------------------------------- */
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+int64_t hpo_mad(const int64_t* y, int64_t n) {
+    if (n <= 0) return 0;
+    int64_t* a = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!a) return -1;
+    for (int64_t i = 0; i < n; ++i) a[i] = y[i] < 0 ? -y[i] : y[i];
+    qsort(a, (size_t)n, sizeof(int64_t), cmp_i64);
+    int64_t v = a[(n - 1) / 2];
+    free(a);
+    return v;
+}
+
+double hpo_sigma_from_mad(int64_t mad) { return HPO_MAD_TO_SIGMA * (double)mad; }
+
+/* ------------------------------------------------------------------------
+ * Steps c5 + c6: matched filtering by a boxcar bank and peak detection
+ * (Section II-B, "Matched Filtering and Peak Detection").
+ * For width W: S(t) = sum_{i=t}^{t+W-1} y(i), 0 <= t <= n - W (int64, formed
+ * by differences of an exact prefix sum).  Sample t is above threshold iff
+ * S(t) >= thr * sigma * sqrt(W) (FP64, products in that order).  Each maximal
+ * run of consecutive above-threshold t gives one candidate at the argmax of
+ * S over the run, ties to the smallest t.  snr = S / (sigma * sqrt(W)).
+ * sigma == 0 gives no candidates.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t dm_idx;
+    int32_t width_idx;
+    int64_t sample;
+    int64_t S;
+    double snr;
+} hpo_raw;
+
+typedef struct {
+    int32_t dm_idx;
+    int32_t width_idx;
+    int64_t sample;
+    double snr;
+    int32_t members;
+    int32_t dm_lo;
+    int32_t dm_hi;
+    int32_t pad_;
+    int64_t t_lo;
+    int64_t t_hi;
+} hpo_cluster;
+
+typedef struct {
+    hpo_raw* v;
+    int64_t n, cap;
+} raw_vec;
+
+static int raw_push(raw_vec* rv, hpo_raw r) {
+    if (rv->n == rv->cap) {
+        int64_t nc = rv->cap ? 2 * rv->cap : 64;
+        hpo_raw* nv = (hpo_raw*)realloc(rv->v, sizeof(hpo_raw) * (size_t)nc);
+        if (!nv) return -1;
+        rv->v = nv;
+        rv->cap = nc;
+    }
+    rv->v[rv->n++] = r;
+    return 0;
+}
+
+static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
+                       const int32_t* widths, int nw, float thr, raw_vec* rv) {
+    if (!(sigma > 0.0)) return 0;
+    int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!P) return -1;
+    P[0] = 0;
+    for (int64_t i = 0; i < n; ++i) P[i + 1] = P[i] + y[i];
+    double thr_d = (double)thr;
+    for (int k = 0; k < nw; ++k) {
+        int64_t W = widths[k];
+        if (W > n) continue;
+        double sw = sqrt((double)W);
+        double lim = thr_d * sigma * sw;
+        int64_t last = n - W;
+        int64_t t = 0;
+        while (t <= last) {
+            int64_t S = P[t + W] - P[t];
+            if ((double)S >= lim) {
+                int64_t best_t = t, best_S = S;
+                ++t;
+                while (t <= last) {
+                    int64_t S2 = P[t + W] - P[t];
+                    if (!((double)S2 >= lim)) break;
+                    if (S2 > best_S) { best_S = S2; best_t = t; }
+                    ++t;
+                }
+                hpo_raw r;
+                r.dm_idx = d;
+                r.width_idx = k;
+                r.sample = best_t;
+                r.S = best_S;
+                r.snr = (double)best_S / (sigma * sw);
+                if (raw_push(rv, r)) { free(P); return -1; }
+            } else {
+                ++t;
+            }
+        }
+    }
+    free(P);
+    return 0;
+}
+
+/* Detection on one baseline-subtracted series y (length n) of trial d. */
+int hpo_detect_trial(const int64_t* y, int64_t n, int d, double sigma,
+                     const int32_t* widths, int nw, float thr,
+                     hpo_raw* out, int64_t cap, int64_t* nout) {
+    raw_vec rv = {0, 0, 0};
+    if (detect_into(y, n, d, sigma, widths, nw, thr, &rv)) { free(rv.v); return HPO_ERR_ARG; }
+    *nout = rv.n;
+    int64_t m = rv.n < cap ? rv.n : cap;
+    if (m > 0) memcpy(out, rv.v, sizeof(hpo_raw) * (size_t)m);
+    free(rv.v);
+    return rv.n > cap ? HPO_ERR_OVERFLOW : HPO_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Step c7: candidate merging and clustering (Section II-B, "Candate Merging
+ * and Clustering"; Algorithm 1, last stage).  Candidates are ordered by
+ * (dm_idx, sample, width_idx).  Two candidates are friends iff
+ * |d_i - d_j| <= dm_tol, |k_i - k_j| <= w_tol and their windows
+ * [t, t + W) lie within t_gap samples of each other:
+ *   max(t_i, t_j) - min(t_i + W_i, t_j + W_j) <= t_gap.
+ * Clusters are the connected components of the friendship graph.  Each
+ * cluster reports its member with maximum snr (ties: smallest key), the member
+ * count, the DM-index range and the time range [min t, max(t + W)).  Clusters
+ * are listed in order of their smallest member key.
+ * ---------------------------------------------------------------------- */
+static int cmp_raw(const void* a, const void* b) {
+    const hpo_raw* x = (const hpo_raw*)a;
+    const hpo_raw* y = (const hpo_raw*)b;
+    if (x->dm_idx != y->dm_idx) return x->dm_idx < y->dm_idx ? -1 : 1;
+    if (x->sample != y->sample) return x->sample < y->sample ? -1 : 1;
+    if (x->width_idx != y->width_idx) return x->width_idx < y->width_idx ? -1 : 1;
+    return 0;
+}
+
+static int64_t uf_find(int64_t* parent, int64_t i) {
+    while (parent[i] != i) {
+        parent[i] = parent[parent[i]];
+        i = parent[i];
+    }
+    return i;
+}
+
+static void uf_union(int64_t* parent, int64_t a, int64_t b) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return;
+    if (a < b) parent[b] = a; else parent[a] = b;   /* root = smallest index */
+}
+
+void hpo_sort_raw(hpo_raw* c, int64_t n) {
+    if (n > 1) qsort(c, (size_t)n, sizeof(hpo_raw), cmp_raw);
+}
+
+int hpo_merge(hpo_raw* c /* sorted in place */, int64_t n, const int32_t* widths,
+              int dm_tol, int64_t t_gap, int w_tol,
+              hpo_cluster* out, int64_t cap, int64_t* nclusters) {
+    *nclusters = 0;
+    if (n <= 0) return HPO_OK;
+    hpo_sort_raw(c, n);
+    int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!parent) return HPO_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) parent[i] = i;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t ti = c[i].sample, ei = ti + widths[c[i].width_idx];
+        for (int64_t j = i + 1; j < n && c[j].dm_idx <= c[i].dm_idx + dm_tol; ++j) {
+            int dk = c[i].width_idx - c[j].width_idx;
+            if (dk < 0) dk = -dk;
+            if (dk > w_tol) continue;
+            int64_t tj = c[j].sample, ej = tj + widths[c[j].width_idx];
+            int64_t gap = (ti > tj ? ti : tj) - (ei < ej ? ei : ej);
+            if (gap <= t_gap) uf_union(parent, i, j);
+        }
+    }
+    int64_t* slot = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!slot) { free(parent); return HPO_ERR_ARG; }
+    int64_t nc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r = uf_find(parent, i);
+        int64_t e = c[i].sample + widths[c[i].width_idx];
+        if (r == i) {
+            slot[i] = nc;
+            if (nc < cap) {
+                hpo_cluster* o = &out[nc];
+                o->dm_idx = c[i].dm_idx;
+                o->width_idx = c[i].width_idx;
+                o->sample = c[i].sample;
+                o->snr = c[i].snr;
+                o->members = 1;
+                o->dm_lo = o->dm_hi = c[i].dm_idx;
+                o->pad_ = 0;
+                o->t_lo = c[i].sample;
+                o->t_hi = e;
+            }
+            ++nc;
+        } else {
+            int64_t s = slot[r];                    /* r < i: already assigned */
+            if (s < cap) {
+                hpo_cluster* o = &out[s];
+                o->members += 1;
+                if (c[i].dm_idx < o->dm_lo) o->dm_lo = c[i].dm_idx;
+                if (c[i].dm_idx > o->dm_hi) o->dm_hi = c[i].dm_idx;
+                if (c[i].sample < o->t_lo) o->t_lo = c[i].sample;
+                if (e > o->t_hi) o->t_hi = e;
+                if (c[i].snr > o->snr) {            /* strict: ties keep the earlier key */
+                    o->dm_idx = c[i].dm_idx;
+                    o->width_idx = c[i].width_idx;
+                    o->sample = c[i].sample;
+                    o->snr = c[i].snr;
+                }
+            }
+        }
+    }
+    free(slot);
+    free(parent);
+    *nclusters = nc;
+    return nc > cap ? HPO_ERR_OVERFLOW : HPO_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * The whole hot path for one filterbank (Algorithm 1 without RFI mitigation):
+ * delays -> dedispersion -> per trial {baseline, MAD sigma, boxcars, peaks}
+ * -> merge.  Trials run in parallel (OpenMP) only for speed; each trial is
+ * independent, as Algorithm 1's per-thread split of the trial loop shows.
+ *
+ * baseline_mode: 0 = running median (remedian), 1 = moving mean.
+ * Window: N = floor(baseline_s / tsamp + 0.5) samples; median mode uses
+ * L = floor(log5 N) levels, mean mode the half-width H = floor(N/2).
+ * Optional outputs (NULL to skip): sigma[ndm], mad[ndm].
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int nchans;
+    double f_top, chan_bw, tsamp;
+    const float* dm_list;
+    int ndm;
+    const int32_t* widths;
+    int nw;
+    float thr;
+    int baseline_mode;
+    double baseline_s;
+    int dm_tol;
+    int64_t t_gap;
+    int w_tol;
+} hpo_params;
+
+int64_t hpo_baseline_window(double baseline_s, double tsamp) {
+    return (int64_t)floor(baseline_s / tsamp + 0.5);
+}
+
+/* Baseline-subtracted series of one trial: y = D - b. */
+int hpo_subtract_baseline(const int32_t* D, int64_t n, int baseline_mode, int64_t win,
+                          int64_t* y) {
+    int64_t* b = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!b) return HPO_ERR_ARG;
+    int rc = baseline_mode == 0 ? hpo_baseline_median(D, n, hpo_remedian_levels(win), b)
+                                : hpo_baseline_mean(D, n, win / 2, b);
+    if (rc == HPO_OK)
+        for (int64_t t = 0; t < n; ++t) y[t] = (int64_t)D[t] - b[t];
+    free(b);
+    return rc;
+}
+
+/* Per-trial stage of Algorithm 1 on an already dedispersed block of rows. */
+int hpo_search_trials(const int32_t* D /* [nrows][nout] */, int64_t nout, int d_begin, int nrows,
+                      const hpo_params* p, hpo_raw* raw, int64_t raw_cap, int64_t* nraw,
+                      double* sigma_out, int64_t* mad_out) {
+    int64_t win = hpo_baseline_window(p->baseline_s, p->tsamp);
+    raw_vec* per = (raw_vec*)calloc((size_t)nrows, sizeof(raw_vec));
+    if (!per) return HPO_ERR_ARG;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+    for (int r = 0; r < nrows; ++r) {
+        int64_t* y = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nout > 0 ? nout : 1));
+        if (!y) { bad = 1; continue; }
+        if (hpo_subtract_baseline(D + (int64_t)r * nout, nout, p->baseline_mode, win, y)) bad = 1;
+        int64_t mad = hpo_mad(y, nout);
+        double sigma = hpo_sigma_from_mad(mad);
+        if (sigma_out) sigma_out[r] = sigma;
+        if (mad_out) mad_out[r] = mad;
+        if (detect_into(y, nout, d_begin + r, sigma, p->widths, p->nw, p->thr, &per[r])) bad = 1;
+        free(y);
+    }
+    int64_t tot = 0;
+    for (int r = 0; r < nrows; ++r) {
+        for (int64_t i = 0; i < per[r].n; ++i) {
+            if (tot < raw_cap) raw[tot] = per[r].v[i];
+            ++tot;
+        }
+        free(per[r].v);
+    }
+    free(per);
+    *nraw = tot;
+    if (bad) return HPO_ERR_ARG;
+    return tot > raw_cap ? HPO_ERR_OVERFLOW : HPO_OK;
+}
+
+int hpo_search(const uint8_t* x, int64_t nsamps, const hpo_params* p,
+               hpo_raw* raw, int64_t raw_cap, int64_t* nraw,
+               hpo_cluster* cl, int64_t cl_cap, int64_t* ncl,
+               double* sigma_out, int64_t* mad_out) {
+    *nraw = 0;
+    *ncl = 0;
+    int32_t* delays = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->ndm * (size_t)p->nchans);
+    if (!delays) return HPO_ERR_ARG;
+    int rc = hpo_delays(p->nchans, p->f_top, p->chan_bw, p->tsamp, p->dm_list, p->ndm, delays);
+    if (rc) { free(delays); return rc; }
+    int32_t maxd = hpo_max_delay(delays, p->ndm, p->nchans);
+    int wmax = 0;
+    for (int k = 0; k < p->nw; ++k) if (p->widths[k] > wmax) wmax = p->widths[k];
+    if (nsamps <= (int64_t)maxd + wmax) { free(delays); return HPO_ERR_SHORT; }
+    int64_t nout = nsamps - maxd;
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->ndm * (size_t)nout);
+    if (!D) { free(delays); return HPO_ERR_ARG; }
+    rc = hpo_dedisperse_rows(x, nsamps, p->nchans, delays, 0, p->ndm, nout, D);
+    free(delays);
+    if (rc) { free(D); return rc; }
+    rc = hpo_search_trials(D, nout, 0, p->ndm, p, raw, raw_cap, nraw, sigma_out, mad_out);
+    free(D);
+    if (rc) return rc;
+    return hpo_merge(raw, *nraw, p->widths, p->dm_tol, p->t_gap, p->w_tol, cl, cl_cap, ncl);
+}

@@ -1,0 +1,67 @@
+"""Mutation test of the oracle pins.
+
+Each case plants one plausible mistake in a copy of ``oracle/hp_oracle.c`` (a
+wrong rounding, a dropped term, an off-by-one, a flipped comparison), builds
+it on the CPU and runs the pin suite against it: every mutant must make at
+least one pin fail.  The mistakes are planted only in the oracle, never in
+the CUDA library.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "hp_oracle.c")
+
+MUTANTS = {
+    "delay_floor": ("(int32_t)rint(sec / tsamp)", "(int32_t)floor(sec / tsamp)"),
+    "delay_ref_infinity": ("(1.0 / (f * f) - inv_top2)", "(1.0 / (f * f))"),
+    "delay_half_channel": ("double f = f_top + (double)c * chan_bw;",
+                           "double f = f_top + ((double)c + 0.5) * chan_bw;"),
+    "dedisp_drop_channel": ("for (int c = 0; c < nchans; ++c) {\n                    int64_t row",
+                            "for (int c = 0; c < nchans - 1; ++c) {\n                    int64_t row"),
+    "dedisp_shift": ("int64_t row = t + dl[c];", "int64_t row = t + dl[c] + (c & 1);"),
+    "remedian_upper": ("return s[(r - 1) / 2];", "return s[r / 2];"),
+    "baseline_trunc": ("b[t] = m[j] + floor_div((m[j + 1] - m[j]) * (t - cj), P);",
+                       "b[t] = m[j] + ((m[j + 1] - m[j]) * (t - cj)) / P;"),
+    "baseline_centre": ("int64_t half = (P - 1) / 2;", "int64_t half = 0;"),
+    "baseline_mean_count": ("b[t] = floor_div(pre[hi + 1] - pre[lo], hi - lo + 1);",
+                            "b[t] = floor_div(pre[hi + 1] - pre[lo], hi - lo + 2);"),
+    "mad_upper": ("int64_t v = a[(n - 1) / 2];", "int64_t v = a[n / 2];"),
+    "sigma_factor": ("HPO_MAD_TO_SIGMA = 1.482602218505602;", "HPO_MAD_TO_SIGMA = 1.0;"),
+    "thr_strict": ("if ((double)S >= lim) {", "if ((double)S > lim) {"),
+    "peak_last_tie": ("if (S2 > best_S) { best_S = S2; best_t = t; }",
+                      "if (S2 >= best_S) { best_S = S2; best_t = t; }"),
+    "snr_no_sqrt": ("r.snr = (double)best_S / (sigma * sw);", "r.snr = (double)best_S / sigma;"),
+    "window_short": ("int64_t S = P[t + W] - P[t];", "int64_t S = P[t + W - 1] - P[t];"),
+    "merge_gap_strict": ("if (gap <= t_gap) uf_union(parent, i, j);",
+                         "if (gap < t_gap) uf_union(parent, i, j);"),
+    "merge_dm_tol": ("c[j].dm_idx <= c[i].dm_idx + dm_tol;", "c[j].dm_idx < c[i].dm_idx + dm_tol;"),
+    "merge_rep_last_tie": ("if (c[i].snr > o->snr) {", "if (c[i].snr >= o->snr) {"),
+    "merge_t_hi": ("if (e > o->t_hi) o->t_hi = e;", "if (c[i].sample > o->t_hi) o->t_hi = c[i].sample;"),
+}
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(SRC) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, source, tmp_path):
+    find, repl = MUTANTS[name]
+    assert source.count(find) == 1, f"mutation site for {name} not unique / missing"
+    csrc = tmp_path / "mutant.c"
+    csrc.write_text(source.replace(find, repl))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", str(csrc), "-o", str(so), "-lm"], check=True)
+    env = dict(os.environ, HPO_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
