@@ -1,0 +1,220 @@
+/*
+ * hp.h -- C ABI of the GB300 single-pulse search library (the data-parallel
+ * hot path of Heimdall++, arXiv 2512.00398).
+ *
+ * Pipeline (Section II-B stage list; Algorithm 1):
+ *   incoherent dedispersion over every trial DM  ->  per trial: baseline
+ *   removal, normalisation, boxcar matched filtering, peak detection  ->
+ *   candidate merging / clustering in (DM, time, width).
+ * RFI mitigation (first GPU stage of Algorithm 1) is not part of this path.
+ *
+ * Conventions shared by every call:
+ *   - Return value: HP_OK (0) or a negative HP_ERR_* code.  Argument errors are
+ *     reported before anything is enqueued.
+ *   - Device pointers are CUDA global-memory addresses on the current device;
+ *     host pointers are ordinary process memory.  Ownership never transfers:
+ *     the caller owns every buffer it passes in, the plan owns its scratch.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously; nothing synchronises the host
+ *     unless the call says so.  Device-side results (counts, statuses) are
+ *     valid once the stream has completed.
+ *   - A plan is not safe for concurrent use from several host threads or on
+ *     several streams at once: calls on one plan must be ordered.
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define HP_OK 0
+#define HP_ERR_INVALID_ARG (-1)      /* bad argument or plan state */
+#define HP_ERR_CUDA (-2)             /* a CUDA runtime call failed */
+#define HP_ERR_OOM (-3)              /* device allocation failed / workspace too small */
+#define HP_ERR_CAND_OVERFLOW (-4)    /* more raw candidates than the plan's capacity */
+#define HP_ERR_TIMEOUT (-5)          /* a bounded device wait gave up */
+#define HP_ERR_NSAMPS_TOO_SHORT (-6) /* nsamps <= max delay + widest boxcar */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* hp_status_str(int status);
+
+/* ------------------------------------------------------------------ types */
+typedef struct hp_plan hp_plan;
+
+/* A merged candidate (one cluster of Section II-B "Candidate Merging and
+ * Clustering"): the member with the highest S/N stands for the cluster.
+ * 48 bytes, natural alignment. */
+typedef struct {
+    int32_t dm_idx;     /* trial index of the representative */
+    int32_t width_idx;  /* boxcar index of the representative */
+    int64_t sample;     /* start of the representative's boxcar, in dedispersed
+                           samples (arrival time at f_top / tsamp) */
+    float snr;          /* representative S/N, S / (sigma * sqrt(W)) */
+    int32_t members;    /* raw candidates in the cluster */
+    int32_t dm_lo;      /* smallest / largest member trial index */
+    int32_t dm_hi;
+    int64_t t_lo;       /* smallest member start sample */
+    int64_t t_hi;       /* largest member boxcar end (start + W, exclusive) */
+} hp_cand;
+
+/* Caller-owned device buffer for merged candidates.  After the stream
+ * completes, *count holds the TRUE number of clusters; only the first
+ * min(*count, capacity) entries are written.  Clusters are ordered by their
+ * smallest member (dm_idx, sample, width_idx). */
+typedef struct {
+    hp_cand* data;      /* device, capacity entries */
+    int64_t capacity;
+    int64_t* count;     /* device, one int64 */
+} hp_cand_buf;
+
+/* A raw (pre-merge) candidate: one maximal above-threshold run of one
+ * (trial, width), placed at the run's largest boxcar sum.  24 bytes. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t width_idx;
+    int64_t sample;     /* boxcar start of the peak */
+    int64_t S;          /* exact integer boxcar sum at the peak */
+} hp_raw_cand;
+
+/* Caller-owned device buffer for raw candidates.  Same count convention as
+ * hp_cand_buf; order is unspecified (hp_merge sorts). */
+typedef struct {
+    hp_raw_cand* data;  /* device, capacity entries */
+    int64_t capacity;
+    int64_t* count;     /* device, one int64 */
+} hp_raw_buf;
+
+/* ------------------------------------------------------------ plan set-up */
+
+/* Create a search plan (host only; no CUDA call is made until the first
+ * search).  Computes the delay table of Section II-B (Eq. 1 with the
+ * cold-plasma law): for channel c at f_c = f_top + c*chan_bw MHz and trial
+ * DM d, delay = rint(4148.808 * DM_d * (f_c^-2 - f_top^-2) / tsamp) samples,
+ * evaluated in FP64.
+ *   nchans        1..65536 channels, channel 0 at f_top_MHz
+ *   chan_bw_MHz   < 0 (frequency falls with channel index); the lowest
+ *                 channel frequency must stay > 0
+ *   tsamp_s       > 0, sampling time in seconds
+ *   dm_list       host, ndm finite values >= 0, non-decreasing (copied)
+ *   boxcar_widths host, nw (1..32) strictly increasing widths in 1..16384 (copied)
+ *   snr_threshold > 0 (finite)
+ * Defaults: running-median baseline over 2.0 s, dm_tol 1, t_gap 0,
+ * w_tol = nw (any width), raw-candidate capacity 2^22.
+ * On error *out is set to NULL. */
+int hp_plan_create(hp_plan** out, int nchans, double f_top_MHz, double chan_bw_MHz,
+                   double tsamp_s, const float* dm_list, int ndm, const int* boxcar_widths,
+                   int nw, float snr_threshold);
+
+/* Release the plan, its device tables and any scratch it allocated itself.
+ * Synchronises the device work it enqueued.  NULL is accepted. */
+int hp_plan_destroy(hp_plan* plan);
+
+/* Tunable parameters (hp_plan_set_param / hp_plan_get_param). */
+#define HP_PARAM_BASELINE_MODE 0  /* 0 = running median (remedian), 1 = moving mean */
+#define HP_PARAM_BASELINE_S 1     /* baseline window in seconds (> 0) */
+#define HP_PARAM_DM_TOL 2         /* merge: max |trial index difference| (>= 0) */
+#define HP_PARAM_T_GAP 3          /* merge: max gap between boxcar windows, samples */
+#define HP_PARAM_W_TOL 4          /* merge: max |width index difference| (>= 0) */
+#define HP_PARAM_RAW_CAPACITY 5   /* raw-candidate scratch capacity (>= 1024) */
+#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1) */
+#define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
+#define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
+
+#define HP_NUM_DEDISP_CONFIGS 4
+
+int hp_plan_set_param(hp_plan* plan, int param, double value);
+int hp_plan_get_param(const hp_plan* plan, int param, double* value);
+
+/* Copy the delay table, int32 [ndm][nchans] row-major, into host memory. */
+int hp_plan_delays(const hp_plan* plan, int32_t* out_host);
+
+/* Largest delay of the table (samples) and the dedispersed length
+ * nout = nsamps - max_delay for a given input length. */
+int hp_plan_max_delay(const hp_plan* plan, int32_t* max_delay);
+
+/* Device scratch needed by hp_search for inputs of nsamps samples. */
+int hp_plan_workspace_bytes(const hp_plan* plan, int64_t nsamps, size_t* bytes);
+
+/* Give the plan a caller-owned device workspace (256-byte aligned, at least
+ * hp_plan_workspace_bytes).  While bound, the plan allocates no scratch (its
+ * constant tables, a few MB, are allocated once by the first search); the
+ * caller keeps ownership and must keep it alive until the plan is destroyed
+ * or another workspace is bound.  Passing NULL unbinds (the plan then
+ * allocates its own scratch with cudaMalloc on demand, grow-only).  The size
+ * depends on the raw capacity and baseline mode: query it after setting them. */
+int hp_plan_bind_workspace(hp_plan* plan, void* workspace_dev, size_t bytes);
+
+/* ----------------------------------------------------------- the hot path */
+
+/* The whole search (Algorithm 1 without RFI mitigation) on one filterbank.
+ *   filterbank_dev  device uint8 [nsamps][nchans], time-major, caller-owned
+ *   nsamps          > max_delay + widest boxcar (else HP_ERR_NSAMPS_TOO_SHORT)
+ *   cand_out        caller-owned merged-candidate buffer
+ * Steps: dedispersion D[d][t] = sum_c x[t + delay(c,d)][c] for
+ * t in [0, nout); per trial the baseline b (HP_PARAM_BASELINE_MODE), y = D - b,
+ * sigma = 1.482602218505602 * median|y|; boxcars S_W(t) = sum_{i<W} y(t+i);
+ * candidates = one per maximal run of S_W(t) >= thr*sigma*sqrt(W) at the run's
+ * largest S (ties: smallest t); friends-of-friends merge.  Asynchronous;
+ * device-side failures (raw-candidate overflow, timeouts) are latched in the
+ * plan and returned by hp_plan_sync_status. */
+int hp_search(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps, void* stream,
+              hp_cand_buf* cand_out);
+
+/* Dedispersion alone (Section II-B, "Incoherent Dedispersion"):
+ *   out_dev  device int32 [ndm][out_pitch], out_pitch >= nout, a multiple of 4;
+ *            samples t >= nout of each row are left untouched. */
+int hp_dedisperse(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps,
+                  int32_t* out_dev, int64_t out_pitch, void* stream);
+
+/* The per-trial stages (baseline removal, normalisation, matched filtering,
+ * peak detection; Algorithm 1's trial loop) on dedispersed series:
+ *   series_dev  device int32 [ndm][pitch], nout valid samples per row
+ *   raw_out     caller-owned raw-candidate buffer (count = true number)
+ *   sigma_dev   optional device double [ndm]: per-trial sigma (NULL to skip)
+ *   mad_dev     optional device int64 [ndm]: per-trial median |y| (NULL to skip) */
+int hp_detect(hp_plan* plan, const int32_t* series_dev, int64_t nout, int64_t pitch,
+              void* stream, hp_raw_buf* raw_out, double* sigma_dev, int64_t* mad_dev);
+
+/* Candidate merging and clustering (Section II-B; Algorithm 1, last stage):
+ *   raw_dev / nraw_dev  device raw candidates and their device count (as
+ *                       written by hp_detect; entries beyond capacity ignored)
+ *   sigma_dev           device double [ndm], per-trial sigma from hp_detect
+ *   cand_out            merged clusters (see hp_cand_buf) */
+int hp_merge(hp_plan* plan, const hp_raw_cand* raw_dev, const int64_t* nraw_dev,
+             int64_t raw_capacity, const double* sigma_dev, void* stream,
+             hp_cand_buf* cand_out);
+
+/* Per-stage timing and launch accounting (no counterpart in the paper, whose
+ * Fig. 2 reports per-stage times of Heimdall).  With HP_PARAM_STAGE_TIMING = 1
+ * every stage launch is bracketed by CUDA events recorded on the launching
+ * stream (up to 4096 launches per stage are kept).  Kernel launches are
+ * counted always. */
+#define HP_STAGE_TRANSPOSE 0    /* time-major -> channel-major copy of the input */
+#define HP_STAGE_DEDISP 1       /* dedispersion kernel */
+#define HP_STAGE_SEARCH 2       /* baseline, sigma, boxcars, peaks */
+#define HP_STAGE_MERGE 3        /* sort + friends-of-friends */
+#define HP_NUM_STAGES 4
+typedef struct {
+    double stage_ms[HP_NUM_STAGES];      /* summed event time of the recorded launches */
+    int64_t stage_calls[HP_NUM_STAGES];  /* launches whose events were summed */
+    int64_t kernel_launches;             /* CUDA kernels launched by the library */
+} hp_stats;
+
+/* Synchronise on the recorded events, write the totals since the last reset
+ * into *out (host), then reset them if `reset` is non-zero. */
+int hp_plan_stats(hp_plan* plan, hp_stats* out, int reset);
+
+/* Wait for the plan's enqueued work on `stream` and return (then clear) the
+ * first device-side status latched since the last call: HP_OK,
+ * HP_ERR_CAND_OVERFLOW or HP_ERR_TIMEOUT.  Synchronises the stream. */
+int hp_plan_sync_status(hp_plan* plan, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HP_H */

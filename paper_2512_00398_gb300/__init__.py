@@ -1,0 +1,275 @@
+"""GB300-native single-pulse search: the data-parallel hot path of Heimdall++
+(arXiv 2512.00398) as hand-written sm_103a CUDA behind a small C ABI.
+
+Python names mirror ``include/hp.h``.  Device buffers are torch CUDA tensors,
+streams are torch CUDA streams (default: the current stream).  The functions
+prefixed ``hp_`` are asynchronous like their C counterparts; ``search``,
+``dedisperse``, ``detect`` and ``merge`` are conveniences that synchronise
+and return host arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ERR_INVALID_ARG,
+                   HP_ERR_NSAMPS_TOO_SHORT, HP_ERR_OOM, HP_ERR_TIMEOUT, HP_NUM_DEDISP_CONFIGS,
+                   HP_NUM_STAGES, HP_OK, HP_PARAM_BASELINE_MODE, HP_PARAM_BASELINE_S,
+                   HP_PARAM_DEDISP_CONFIG, HP_PARAM_DM_TOL, HP_PARAM_RAW_CAPACITY,
+                   HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
+                   HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
+                   STAGE_NAMES, CandBuf, HPError, Stats, check, lib, status_str)
+
+_PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASELINE_S,
+           "dm_tol": HP_PARAM_DM_TOL, "t_gap": HP_PARAM_T_GAP, "w_tol": HP_PARAM_W_TOL,
+           "raw_capacity": HP_PARAM_RAW_CAPACITY, "dedisp_config": HP_PARAM_DEDISP_CONFIG,
+           "stage_timing": HP_PARAM_STAGE_TIMING, "timeout_s": HP_PARAM_TIMEOUT_S}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+class Plan:
+    """Owning handle of an ``hp_plan`` (see ``hp_plan_create``)."""
+
+    def __init__(self, nchans, f_top, chan_bw, tsamp, dm_list, widths, snr_threshold, **params):
+        self.dm_list = np.ascontiguousarray(dm_list, dtype=np.float32)
+        self.widths = np.ascontiguousarray(widths, dtype=np.int32)
+        self.nchans = int(nchans)
+        self.f_top, self.chan_bw, self.tsamp = float(f_top), float(chan_bw), float(tsamp)
+        self.threshold = float(snr_threshold)
+        h = C.c_void_p()
+        check(lib().hp_plan_create(C.byref(h), self.nchans, self.f_top, self.chan_bw,
+                                   self.tsamp, self.dm_list.ctypes.data_as(C.c_void_p),
+                                   int(self.dm_list.size), self.widths.ctypes.data_as(C.c_void_p),
+                                   int(self.widths.size), C.c_float(self.threshold)),
+              "hp_plan_create")
+        self._h = h
+        self._ws = None
+        for k, v in params.items():
+            self.set_param(k, v)
+
+    # -- handle ----------------------------------------------------------
+    @property
+    def handle(self):
+        if self._h is None:
+            raise HPError(HP_ERR_INVALID_ARG, "plan already destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().hp_plan_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- parameters ------------------------------------------------------
+    @property
+    def ndm(self) -> int:
+        return int(self.dm_list.size)
+
+    @property
+    def nw(self) -> int:
+        return int(self.widths.size)
+
+    def set_param(self, name, value):
+        pid = _PARAMS[name] if isinstance(name, str) else int(name)
+        check(lib().hp_plan_set_param(self.handle, pid, float(value)), f"hp_plan_set_param({name})")
+
+    def get_param(self, name) -> float:
+        pid = _PARAMS[name] if isinstance(name, str) else int(name)
+        v = C.c_double()
+        check(lib().hp_plan_get_param(self.handle, pid, C.byref(v)), f"hp_plan_get_param({name})")
+        return v.value
+
+    def delays(self) -> np.ndarray:
+        out = np.empty((self.ndm, self.nchans), dtype=np.int32)
+        check(lib().hp_plan_delays(self.handle, out.ctypes.data_as(C.c_void_p)), "hp_plan_delays")
+        return out
+
+    @property
+    def max_delay(self) -> int:
+        v = C.c_int32()
+        check(lib().hp_plan_max_delay(self.handle, C.byref(v)), "hp_plan_max_delay")
+        return int(v.value)
+
+    def nout(self, nsamps: int) -> int:
+        return int(nsamps) - self.max_delay
+
+    def workspace_bytes(self, nsamps: int) -> int:
+        v = C.c_size_t()
+        check(lib().hp_plan_workspace_bytes(self.handle, int(nsamps), C.byref(v)),
+              "hp_plan_workspace_bytes")
+        return int(v.value)
+
+    def bind_workspace(self, nsamps: int, device=None):
+        """Allocate the scratch for inputs of ``nsamps`` samples as a torch
+        tensor and bind it, so the library itself allocates nothing."""
+        torch = _torch()
+        need = self.workspace_bytes(nsamps)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = None
+            dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+            self._ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        check(lib().hp_plan_bind_workspace(self.handle, C.c_void_p(self._ws.data_ptr()),
+                                           self._ws.numel()), "hp_plan_bind_workspace")
+        return self._ws
+
+
+# ------------------------------------------------------------------ C names
+def hp_plan_create(nchans, f_top_MHz, chan_bw_MHz, tsamp_s, dm_list, boxcar_widths,
+                   snr_threshold, **params) -> Plan:
+    return Plan(nchans, f_top_MHz, chan_bw_MHz, tsamp_s, dm_list, boxcar_widths, snr_threshold,
+                **params)
+
+
+def hp_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def _check_fb(plan: Plan, fb):
+    torch = _torch()
+    if not (isinstance(fb, torch.Tensor) and fb.is_cuda and fb.dtype == torch.uint8
+            and fb.dim() == 2 and fb.shape[1] == plan.nchans and fb.is_contiguous()):
+        raise HPError(HP_ERR_INVALID_ARG, "filterbank must be a contiguous CUDA uint8 "
+                                          "tensor [nsamps, nchans]")
+
+
+def new_cand_buf(capacity: int, device=None):
+    """Device storage for ``capacity`` hp_cand records plus their count."""
+    torch = _torch()
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    data = torch.empty(max(1, capacity) * CAND_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    return data, count
+
+
+def _buf(data, count, capacity) -> CandBuf:
+    return CandBuf(C.c_void_p(data.data_ptr()), int(capacity), C.c_void_p(count.data_ptr()))
+
+
+def hp_search(plan: Plan, filterbank, stream=None, out=None, capacity: int = 1 << 16):
+    """Enqueue the whole search; returns the device (data, count) pair."""
+    _check_fb(plan, filterbank)
+    data, count = out if out is not None else new_cand_buf(capacity, filterbank.device)
+    cap = data.numel() // CAND_DTYPE.itemsize
+    b = _buf(data, count, cap)
+    check(lib().hp_search(plan.handle, C.c_void_p(filterbank.data_ptr()), int(filterbank.shape[0]),
+                          _stream_ptr(stream), C.byref(b)), "hp_search")
+    return data, count
+
+
+def hp_dedisperse(plan: Plan, filterbank, stream=None, out=None):
+    """Enqueue dedispersion; returns an int32 [ndm, pitch] tensor (nout valid)."""
+    torch = _torch()
+    _check_fb(plan, filterbank)
+    nout = plan.nout(filterbank.shape[0])
+    if out is None:
+        pitch = (nout + 3) // 4 * 4
+        out = torch.empty((plan.ndm, pitch), dtype=torch.int32, device=filterbank.device)
+    check(lib().hp_dedisperse(plan.handle, C.c_void_p(filterbank.data_ptr()),
+                              int(filterbank.shape[0]), C.c_void_p(out.data_ptr()),
+                              int(out.stride(0)), _stream_ptr(stream)), "hp_dedisperse")
+    return out
+
+
+def hp_detect(plan: Plan, series, nout: int, stream=None, capacity: int = 1 << 20):
+    """Enqueue the per-trial stages on dedispersed rows; returns
+    (raw data, raw count, sigma, mad) device tensors."""
+    torch = _torch()
+    dev = series.device
+    raw = torch.empty(max(1, capacity) * RAW_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    sigma = torch.empty(plan.ndm, dtype=torch.float64, device=dev)
+    mad = torch.empty(plan.ndm, dtype=torch.int64, device=dev)
+    b = CandBuf(C.c_void_p(raw.data_ptr()), int(capacity), C.c_void_p(cnt.data_ptr()))
+    check(lib().hp_detect(plan.handle, C.c_void_p(series.data_ptr()), int(nout),
+                          int(series.stride(0)), _stream_ptr(stream), C.byref(b),
+                          C.c_void_p(sigma.data_ptr()), C.c_void_p(mad.data_ptr())), "hp_detect")
+    return raw, cnt, sigma, mad
+
+
+def hp_merge(plan: Plan, raw, raw_count, sigma, stream=None, out=None, capacity: int = 1 << 16):
+    """Enqueue merging of device raw candidates; returns (data, count)."""
+    data, count = out if out is not None else new_cand_buf(capacity, raw.device)
+    cap = data.numel() // CAND_DTYPE.itemsize
+    b = _buf(data, count, cap)
+    raw_cap = raw.numel() // RAW_DTYPE.itemsize
+    check(lib().hp_merge(plan.handle, C.c_void_p(raw.data_ptr()), C.c_void_p(raw_count.data_ptr()),
+                         int(raw_cap), C.c_void_p(sigma.data_ptr()), _stream_ptr(stream),
+                         C.byref(b)), "hp_merge")
+    return data, count
+
+
+def hp_plan_sync_status(plan: Plan, stream=None) -> int:
+    return int(lib().hp_plan_sync_status(plan.handle, _stream_ptr(stream)))
+
+
+def hp_plan_stats(plan: Plan, reset: bool = True) -> dict:
+    """Per-stage event times (ms, summed) and launch counts since the last reset."""
+    st = Stats()
+    check(lib().hp_plan_stats(plan.handle, C.byref(st), int(bool(reset))), "hp_plan_stats")
+    return {"stage_ms": {n: st.stage_ms[i] for i, n in enumerate(STAGE_NAMES)},
+            "stage_calls": {n: int(st.stage_calls[i]) for i, n in enumerate(STAGE_NAMES)},
+            "kernel_launches": int(st.kernel_launches)}
+
+
+# ------------------------------------------------------- host conveniences
+def cands_to_numpy(data, count, dtype=CAND_DTYPE) -> np.ndarray:
+    n = int(count.item())
+    cap = data.numel() // dtype.itemsize
+    m = min(n, cap)
+    host = data[: m * dtype.itemsize].cpu().numpy()
+    return host.view(dtype).copy()
+
+
+def search(plan: Plan, filterbank, stream=None, capacity: int = 1 << 16) -> np.ndarray:
+    """Search and return the merged candidates (synchronises)."""
+    data, count = hp_search(plan, filterbank, stream, capacity=capacity)
+    st = hp_plan_sync_status(plan, stream)
+    if st != HP_OK:
+        raise HPError(st, "hp_search (device)")
+    n = int(count.item())
+    if n > capacity:
+        raise HPError(HP_ERR_CAND_OVERFLOW, f"hp_search: {n} clusters > capacity {capacity}")
+    return cands_to_numpy(data, count)
+
+
+def dedisperse(plan: Plan, filterbank, stream=None) -> np.ndarray:
+    out = hp_dedisperse(plan, filterbank, stream)
+    st = hp_plan_sync_status(plan, stream)
+    if st != HP_OK:
+        raise HPError(st, "hp_dedisperse (device)")
+    return out[:, : plan.nout(filterbank.shape[0])].cpu().numpy()
+
+
+def detect(plan: Plan, series, nout: int, stream=None, capacity: int = 1 << 20):
+    raw, cnt, sigma, mad = hp_detect(plan, series, nout, stream, capacity)
+    st = hp_plan_sync_status(plan, stream)
+    if st != HP_OK:
+        raise HPError(st, "hp_detect (device)")
+    n = int(cnt.item())
+    if n > capacity:
+        raise HPError(HP_ERR_CAND_OVERFLOW, f"hp_detect: {n} raw candidates > {capacity}")
+    return cands_to_numpy(raw, cnt, RAW_DTYPE), sigma.cpu().numpy(), mad.cpu().numpy()

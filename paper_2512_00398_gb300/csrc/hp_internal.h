@@ -1,0 +1,172 @@
+// hp_internal.h -- plan object, device table layouts and kernel launchers of
+// the search library.  Host code (plan.cpp) and the .cu files share this
+// header; nothing here is part of the public C ABI (include/hp.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hp.h"
+
+namespace hp {
+
+// ------------------------------------------------------------------ limits
+constexpr int kMaxChans = 65536;
+constexpr int kMaxWidths = 32;
+constexpr int kMaxWidth = 16384;         // widest boxcar (detect tile halo in shared memory)
+constexpr int kMaxDMs = 1 << 20;
+constexpr int kStageMaxChans = 256;      // 16-bit lanes hold <= 257 sums of bytes
+constexpr int kHistFine = 4096;          // |y| < 4096 binned exactly
+constexpr int kHistBins = 8192;          // + 4096 coarse bins of |y| >> 12
+constexpr int kDetectTile = 4096;        // boxcar starts per detect block
+constexpr int kSortChunk = 2048;         // keys sorted per block before merging
+constexpr int kKeyDmShift = 43;          // sort key: dm << 43 | sample << 5 | width
+constexpr int kKeySampleShift = 5;
+constexpr int64_t kMaxSamples = (int64_t)1 << 38;
+
+// ------------------------------------------------------ dedispersion tiles
+// Thread tile: RD trials x NW words (4 samples each) per thread; WD warps
+// along the trial axis, WT along time.  BD = WD*RD trials, BT = WT*NW*128
+// samples per block.
+struct DedispConfig {
+    int RD, NW, WD, WT;
+    int stage_bytes;   // shared memory per pipeline stage (two stages per block)
+    int BD() const { return WD * RD; }
+    int BT() const { return WT * NW * 128; }
+};
+constexpr int kNumDedispConfigs = 4;
+extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
+
+// One staged channel row of a DM tile (16 bytes, copied into shared memory).
+struct ChanDesc {
+    uint32_t c;        // channel index
+    int32_t goff;      // first input sample of the row relative to the time tile
+    uint32_t offB;     // byte offset of the row copy in the stage buffer
+    uint32_t nwords;   // 4-byte words per shifted variant
+};
+static_assert(sizeof(ChanDesc) == 16, "ChanDesc layout");
+
+struct StageDesc {
+    uint32_t chan_begin;  // index into the channel-descriptor array
+    uint32_t nchan;
+    uint32_t addr_off;    // byte offset of the word-address table in the buffer
+    uint32_t tx_bytes;    // bytes landing in shared memory for this stage
+};
+
+struct TileDesc {
+    int32_t d0, nd;            // first trial, trial count (<= BD)
+    int32_t stage_begin, nstages;
+};
+
+// Host copy of the tiling of one plan for one config.
+struct DedispTiling {
+    int cfg = -1;
+    int BD = 0, BT = 0;
+    std::vector<TileDesc> tiles;
+    std::vector<StageDesc> stages;
+    std::vector<ChanDesc> chans;
+    std::vector<uint16_t> addr;    // [chan desc][BD] word addresses in the stage buffer
+    int64_t max_reach = 0;         // max over rows of goff + row bytes
+};
+
+// Device view of one dedispersion job (one filterbank).
+struct DedispJob {
+    const uint8_t* xt;         // transposed input [nchans][xt_pitch]
+    int64_t xt_pitch;
+    int32_t* out;              // [ndm][out_pitch]
+    int64_t out_pitch;
+    int64_t nout;
+    int32_t ntt;               // time tiles
+    int32_t ndt;               // DM tiles
+    const TileDesc* tiles;
+    const StageDesc* stages;
+    const ChanDesc* chans;
+    const uint16_t* addr;
+};
+
+// Jobs of one dedispersion launch, passed by value as the kernel parameter.
+// Block b works on item b - prefix[j] of the job j with prefix[j] <= b < prefix[j+1];
+// item i of a job is (DM tile i / ntt, time tile i % ntt).
+constexpr int kMaxJobs = 32;
+struct DedispBatch {
+    int32_t njobs;
+    int32_t pad_;
+    int64_t prefix[kMaxJobs + 1];
+    DedispJob jobs[kMaxJobs];
+};
+
+// ------------------------------------------------------------- launchers
+// All return cudaSuccess or the launch error.
+cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
+                             int64_t xt_pitch, cudaStream_t s);
+cudaError_t launch_dedisp(int cfg, const DedispBatch& batch, int* status, uint64_t timeout_ns,
+                          cudaStream_t s);
+
+struct SearchArgs {
+    const int32_t* D;          // [ndm][pitch]
+    int64_t pitch, nout;
+    int ndm;
+    int nw;
+    const int32_t* widths;     // device [nw]
+    int32_t wmax;
+    float thr;
+    int baseline_mode;         // 0 median, 1 mean
+    int levels;                // remedian levels (median mode)
+    int64_t win;               // window in samples (mean mode half width = win/2)
+    // scratch (device)
+    int32_t* lvl_a;            // remedian pass buffers [ndm][lvl_pitch]
+    int32_t* lvl_b;
+    int64_t lvl_pitch_a, lvl_pitch_b;
+    int64_t* mean_pre;         // mean mode block prefix [ndm][mean_pitch]
+    int64_t mean_pitch;
+    uint32_t* hist;            // [ndm][kHistBins]
+    int32_t* refine_bucket;    // [ndm]
+    int64_t* refine_rank;      // [ndm]
+    int64_t* mad;              // [ndm]
+    double* sigma;             // [ndm]
+    int64_t* tint;             // [ndm][nw] integer thresholds
+    hp_raw_cand* raw;          // output
+    int64_t raw_cap;
+    int64_t* raw_count;
+    int* status;
+};
+cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch);
+
+struct MergeArgs {
+    const hp_raw_cand* raw;
+    const int64_t* nraw;
+    int64_t cap;               // capacity of raw (== of every scratch array below)
+    const double* sigma;       // [ndm]
+    const int32_t* widths;     // device [nw]
+    int nw;
+    int32_t wmax;
+    int dm_tol;
+    int64_t t_gap;
+    int w_tol;
+    // scratch
+    uint64_t* keys[2];
+    int64_t* vals[2];
+    int32_t* parent;
+    uint64_t* best_bits;
+    int32_t* rep;
+    int32_t* members;
+    int32_t* dm_lo;
+    int32_t* dm_hi;
+    unsigned long long* t_lo;
+    unsigned long long* t_hi;
+    int32_t* scan;             // [cap]
+    int32_t* block_sums;       // [cap / 1024 + 1]
+    int64_t* n_clamped;        // one int64
+    hp_cand* out;
+    int64_t out_cap;
+    int64_t* out_count;
+    int* status;
+};
+cudaError_t launch_merge(const MergeArgs& a, cudaStream_t s, int64_t* nlaunch);
+
+int merge_sort_passes(int64_t cap);
+
+}  // namespace hp

@@ -1,0 +1,808 @@
+// plan.cpp -- host side of the search library: argument checking, the delay
+// table (Section II-B, Eq. 1 with the cold-plasma law), the dedispersion
+// tiling, workspace layout and the C ABI entry points of include/hp.h.
+//
+// Compiled with -ffp-contract=off: the delay table is evaluated in FP64 with
+// one fixed expression order and no fused multiply-add.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hp_internal.h"
+
+using namespace hp;
+
+namespace {
+
+constexpr double kKDM = 4148.808;   // s MHz^2 pc^-1 cm^3
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int64_t round_up64(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int64_t nsamps = 0, nout = 0;
+    int64_t xt_pitch = 0, dpitch = 0;
+    int64_t lvl_pitch_a = 0, lvl_pitch_b = 0, mean_pitch = 0;
+    size_t xt = 0, D = 0, lvl_a = 0, lvl_b = 0, mean = 0, hist = 0, rbucket = 0, rrank = 0,
+           mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
+           vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
+           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0;
+    size_t total = 0;
+    size_t search_begin = 0;   // everything from here on is search/merge scratch
+};
+
+}  // namespace
+
+struct hp_plan {
+    int nchans = 0;
+    double f_top = 0, chan_bw = 0, tsamp = 0;
+    std::vector<float> dm_list;
+    std::vector<int32_t> widths;
+    float thr = 0;
+    int baseline_mode = 0;
+    double baseline_s = 2.0;
+    int dm_tol = 1;
+    int64_t t_gap = 0;
+    int w_tol = 0;
+    int64_t raw_capacity = (int64_t)1 << 22;
+    int dedisp_cfg = 0;
+    uint64_t timeout_ns = 1000000000ull;
+
+    std::vector<int32_t> delays;   // [ndm][nchans]
+    int32_t maxd = 0, wmax = 0;
+
+    DedispTiling tiling;           // for dedisp_cfg
+
+    // device state
+    int device = -1;
+    void* tables = nullptr;        // plan-owned constant tables + status word
+    size_t tables_bytes = 0;
+    int tables_cfg = -1;
+    int* status = nullptr;
+    const TileDesc* d_tiles = nullptr;
+    const StageDesc* d_stages = nullptr;
+    const ChanDesc* d_chans = nullptr;
+    const uint16_t* d_addr = nullptr;
+    int32_t* d_widths = nullptr;
+
+    void* ws_user = nullptr;
+    size_t ws_user_bytes = 0;
+    void* ws_own = nullptr;
+    size_t ws_own_bytes = 0;
+
+    // stage timing (events on the launching stream) and launch accounting
+    bool timing = false;
+    std::vector<cudaEvent_t> ev[HP_NUM_STAGES];   // pairs (begin, end)
+    int ev_used[HP_NUM_STAGES] = {0, 0, 0, 0};
+    int64_t launches = 0;
+
+    int ndm() const { return (int)dm_list.size(); }
+    int nw() const { return (int)widths.size(); }
+};
+
+namespace {
+
+int check_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return HP_OK;
+    if (e == cudaErrorMemoryAllocation) return HP_ERR_OOM;
+    return HP_ERR_CUDA;
+}
+
+constexpr int kMaxTimedLaunches = 4096;
+
+// Record the begin event of a stage launch; returns the pair index or -1.
+int stage_begin(hp_plan* p, int stage, cudaStream_t s) {
+    if (!p->timing || p->ev_used[stage] >= kMaxTimedLaunches) return -1;
+    const int i = p->ev_used[stage];
+    std::vector<cudaEvent_t>& v = p->ev[stage];
+    while ((int)v.size() < 2 * (i + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        v.push_back(e);
+    }
+    if (cudaEventRecord(v[2 * i], s) != cudaSuccess) return -1;
+    return i;
+}
+
+void stage_end(hp_plan* p, int stage, int i, cudaStream_t s) {
+    if (i < 0) return;
+    if (cudaEventRecord(p->ev[stage][2 * i + 1], s) == cudaSuccess) p->ev_used[stage] = i + 1;
+}
+
+// ---------------------------------------------------------------- delays
+void compute_delays(hp_plan* p) {
+    const int ndm = p->ndm(), nch = p->nchans;
+    p->delays.assign((size_t)ndm * nch, 0);
+    const double inv_top2 = 1.0 / (p->f_top * p->f_top);
+    int32_t mx = 0;
+    for (int d = 0; d < ndm; ++d) {
+        const double dm = (double)p->dm_list[d];
+        for (int c = 0; c < nch; ++c) {
+            const double f = p->f_top + (double)c * p->chan_bw;
+            const double sec = kKDM * dm * (1.0 / (f * f) - inv_top2);
+            const int32_t v = (int32_t)std::rint(sec / p->tsamp);
+            p->delays[(size_t)d * nch + c] = v;
+            mx = std::max(mx, v);
+        }
+    }
+    p->maxd = mx;
+}
+
+// ------------------------------------------------------- dedispersion tiling
+// A DM tile holds up to BD consecutive trials.  For every channel the block
+// stages the input row window [t0 + base, t0 + base + 4*nwords + 4) where
+// base = delay(c, first trial) rounded down to 16 bytes; a trial j of the tile
+// then reads 4-byte words at byte offset rel = delay(c, j) - base, served from
+// one of four byte-shifted copies of the row (rel & 3) so every read is an
+// aligned word.  Channels are packed into stages that fit the stage buffer.
+struct RowGeom {
+    int32_t base;
+    uint32_t nwords, bbytes, smem;
+};
+
+RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT) {
+    RowGeom g;
+    const int32_t lo = p->delays[(size_t)d0 * p->nchans + c];
+    const int32_t hi = p->delays[(size_t)(d0 + nd - 1) * p->nchans + c];
+    g.base = lo & ~15;
+    const uint32_t span = (uint32_t)(hi - g.base);
+    g.nwords = (span >> 2) + (uint32_t)(BT / 4);
+    g.bbytes = (uint32_t)align_up(4 * (size_t)g.nwords + 4, 16);
+    g.smem = g.bbytes + (uint32_t)align_up(12 * (size_t)g.nwords, 16);
+    return g;
+}
+
+uint32_t stage_header(int nchan, int BD) {
+    return (uint32_t)(align_up((size_t)nchan * sizeof(ChanDesc), 16) +
+                      align_up((size_t)nchan * BD * sizeof(uint16_t), 16));
+}
+
+int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
+    const DedispConfig& C = kDedispConfigs[cfg];
+    const int BD = C.BD(), BT = C.BT();
+    const uint32_t budget = (uint32_t)C.stage_bytes;
+    const int ndm = p->ndm(), nch = p->nchans;
+    T->cfg = cfg;
+    T->BD = BD;
+    T->BT = BT;
+    T->tiles.clear();
+    T->stages.clear();
+    T->chans.clear();
+    T->addr.clear();
+    T->max_reach = 0;
+    int d0 = 0;
+    while (d0 < ndm) {
+        // grow the tile while every channel row alone still fits a stage
+        int nd = 1;
+        while (nd < BD && d0 + nd < ndm) {
+            bool ok = true;
+            for (int c = nch - 1; c >= 0 && ok; --c)
+                ok = row_geom(p, d0, nd + 1, c, BT).smem + stage_header(1, BD) <= budget;
+            if (!ok) break;
+            ++nd;
+        }
+        for (int c = 0; c < nch; ++c)
+            if (row_geom(p, d0, nd, c, BT).smem + stage_header(1, BD) > budget) return HP_ERR_INVALID_ARG;
+        TileDesc td;
+        td.d0 = d0;
+        td.nd = nd;
+        td.stage_begin = (int32_t)T->stages.size();
+        td.nstages = 0;
+        int c = 0;
+        while (c < nch) {
+            int n = 0;
+            uint32_t rows = 0;
+            while (c + n < nch && n < kStageMaxChans) {
+                const RowGeom g = row_geom(p, d0, nd, c + n, BT);
+                if (stage_header(n + 1, BD) + rows + g.smem > budget) break;
+                rows += g.smem;
+                ++n;
+            }
+            StageDesc sd;
+            sd.chan_begin = (uint32_t)T->chans.size();
+            sd.nchan = (uint32_t)n;
+            sd.addr_off = (uint32_t)align_up((size_t)n * sizeof(ChanDesc), 16);
+            uint32_t off = stage_header(n, BD);
+            uint32_t tx = (uint32_t)(n * sizeof(ChanDesc) + n * BD * sizeof(uint16_t));
+            for (int i = 0; i < n; ++i) {
+                const int cc = c + i;
+                const RowGeom g = row_geom(p, d0, nd, cc, BT);
+                ChanDesc cd;
+                cd.c = (uint32_t)cc;
+                cd.goff = g.base;
+                cd.offB = off;
+                cd.nwords = g.nwords;
+                T->chans.push_back(cd);
+                const uint32_t offV = off + g.bbytes;
+                for (int j = 0; j < BD; ++j) {
+                    const int jj = j < nd ? j : 0;
+                    const int32_t rel =
+                        p->delays[(size_t)(d0 + jj) * nch + cc] - g.base;
+                    const uint32_t r = (uint32_t)rel & 3u;
+                    const uint32_t vb = r == 0 ? off : offV + (r - 1) * 4 * g.nwords;
+                    const uint32_t byte_addr = vb + 4 * ((uint32_t)rel >> 2);
+                    T->addr.push_back((uint16_t)(byte_addr >> 2));
+                }
+                tx += g.bbytes;
+                off += g.smem;
+                T->max_reach = std::max<int64_t>(T->max_reach, (int64_t)g.base + g.bbytes);
+            }
+            if (off > budget || (off >> 2) > 0xFFFF) return HP_ERR_INVALID_ARG;
+            sd.tx_bytes = tx;
+            T->stages.push_back(sd);
+            td.nstages++;
+            c += n;
+        }
+        T->tiles.push_back(td);
+        d0 += nd;
+    }
+    return HP_OK;
+}
+
+// ------------------------------------------------------------- workspace
+int64_t xt_pitch_for(int64_t nsamps) {
+    int bt_max = 0;
+    for (int i = 0; i < kNumDedispConfigs; ++i) bt_max = std::max(bt_max, kDedispConfigs[i].BT());
+    return round_up64(nsamps + bt_max + 32, 16);
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int64_t baseline_window(const hp_plan* p) {
+    return (int64_t)std::floor(p->baseline_s / p->tsamp + 0.5);
+}
+
+int remedian_levels(int64_t win) {
+    int L = 0;
+    int64_t q = 1;
+    while (win >= 1 && q <= win / 5) {
+        q *= 5;
+        ++L;
+    }
+    return L;
+}
+
+Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
+    Layout L;
+    L.nsamps = nsamps;
+    L.nout = nsamps - p->maxd;
+    const int ndm = p->ndm();
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    if (with_dedisp) {
+        L.xt_pitch = xt_pitch_for(nsamps);
+        L.dpitch = round_up64(L.nout, 64);
+        L.xt = take((size_t)p->nchans * L.xt_pitch);
+        L.D = take((size_t)ndm * L.dpitch * 4);
+    }
+    L.search_begin = off;
+    // remedian passes of up to five levels: pass 1 writes buffer a, pass 2
+    // buffer b, later passes alternate (each pass shrinks the series)
+    const int levels = remedian_levels(baseline_window(p));
+    const int q1 = std::min(levels, 5), q2 = std::min(std::max(levels - 5, 0), 5);
+    int64_t p1 = 1, p2 = 1;
+    for (int i = 0; i < q1; ++i) p1 *= 5;
+    for (int i = 0; i < q2; ++i) p2 *= 5;
+    const int64_t n1 = ceil_div(std::max<int64_t>(L.nout, 1), p1);
+    L.lvl_pitch_a = round_up64(std::max<int64_t>(n1, 1), 4);
+    L.lvl_pitch_b = round_up64(std::max<int64_t>(ceil_div(n1, p2), 1), 4);
+    L.lvl_a = take((size_t)ndm * L.lvl_pitch_a * 4);
+    L.lvl_b = take((size_t)ndm * L.lvl_pitch_b * 4);
+    L.mean_pitch = ceil_div(std::max<int64_t>(L.nout, 1), 32) + 1;
+    L.mean = take(p->baseline_mode == 1 ? (size_t)ndm * L.mean_pitch * 8 : 0);
+    L.hist = take((size_t)ndm * kHistBins * 4);
+    L.rbucket = take((size_t)ndm * 4);
+    L.rrank = take((size_t)ndm * 8);
+    L.mad = take((size_t)ndm * 8);
+    L.sigma = take((size_t)ndm * 8);
+    L.tint = take((size_t)ndm * p->nw() * 8);
+    const size_t cap = (size_t)p->raw_capacity;
+    // the sort works on whole chunks: key/value scratch is padded to a chunk multiple
+    const size_t cap_pad = align_up(cap, (size_t)kSortChunk);
+    L.raw = take(cap * sizeof(hp_raw_cand));
+    L.raw_count = take(8);
+    L.keys0 = take(cap_pad * 8);
+    L.keys1 = take(cap_pad * 8);
+    L.vals0 = take(cap_pad * 8);
+    L.vals1 = take(cap_pad * 8);
+    L.parent = take(cap * 4);
+    L.best = take(cap * 8);
+    L.rep = take(cap * 4);
+    L.members = take(cap * 4);
+    L.dmlo = take(cap * 4);
+    L.dmhi = take(cap * 4);
+    L.tlo = take(cap * 8);
+    L.thi = take(cap * 8);
+    L.scan = take(cap * 4);
+    L.bsums = take((cap / 1024 + 2) * 4);
+    L.nclamp = take(8);
+    L.total = off;
+    return L;
+}
+
+int ensure_device_tables(hp_plan* p) {
+    if (p->tables && p->tables_cfg == p->dedisp_cfg) return HP_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HP_ERR_CUDA;
+    if (p->tiling.cfg != p->dedisp_cfg) {
+        int rc = build_tiling(p, p->dedisp_cfg, &p->tiling);
+        if (rc) return rc;
+    }
+    const DedispTiling& T = p->tiling;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    const size_t o_status = take(256);
+    const size_t o_tiles = take(T.tiles.size() * sizeof(TileDesc));
+    const size_t o_stages = take(T.stages.size() * sizeof(StageDesc));
+    const size_t o_chans = take(T.chans.size() * sizeof(ChanDesc));
+    const size_t o_addr = take(T.addr.size() * sizeof(uint16_t));
+    const size_t o_widths = take(p->widths.size() * sizeof(int32_t));
+    const size_t total = off;
+    int prev_status = 0;
+    if (p->tables) {
+        if (p->status) cudaMemcpy(&prev_status, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaDeviceSynchronize();
+        cudaFree(p->tables);
+        p->tables = nullptr;
+    }
+    void* mem = nullptr;
+    int rc = check_cuda(cudaMalloc(&mem, total));
+    if (rc) return rc;
+    std::vector<uint8_t> host(total, 0);
+    std::memcpy(host.data() + o_status, &prev_status, sizeof(int));
+    std::memcpy(host.data() + o_tiles, T.tiles.data(), T.tiles.size() * sizeof(TileDesc));
+    std::memcpy(host.data() + o_stages, T.stages.data(), T.stages.size() * sizeof(StageDesc));
+    std::memcpy(host.data() + o_chans, T.chans.data(), T.chans.size() * sizeof(ChanDesc));
+    std::memcpy(host.data() + o_addr, T.addr.data(), T.addr.size() * sizeof(uint16_t));
+    std::memcpy(host.data() + o_widths, p->widths.data(), p->widths.size() * sizeof(int32_t));
+    rc = check_cuda(cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice));
+    if (rc) {
+        cudaFree(mem);
+        return rc;
+    }
+    uint8_t* b = (uint8_t*)mem;
+    p->tables = mem;
+    p->tables_bytes = total;
+    p->tables_cfg = p->dedisp_cfg;
+    p->device = dev;
+    p->status = (int*)(b + o_status);
+    p->d_tiles = (const TileDesc*)(b + o_tiles);
+    p->d_stages = (const StageDesc*)(b + o_stages);
+    p->d_chans = (const ChanDesc*)(b + o_chans);
+    p->d_addr = (const uint16_t*)(b + o_addr);
+    p->d_widths = (int32_t*)(b + o_widths);
+    return HP_OK;
+}
+
+int ensure_workspace(hp_plan* p, size_t need, uint8_t** base) {
+    if (p->ws_user) {
+        if (p->ws_user_bytes < need) return HP_ERR_OOM;
+        *base = (uint8_t*)p->ws_user;
+        return HP_OK;
+    }
+    if (p->ws_own_bytes < need) {
+        if (p->ws_own) {
+            cudaDeviceSynchronize();
+            cudaFree(p->ws_own);
+            p->ws_own = nullptr;
+            p->ws_own_bytes = 0;
+        }
+        int rc = check_cuda(cudaMalloc(&p->ws_own, need));
+        if (rc) return rc;
+        p->ws_own_bytes = need;
+    }
+    *base = (uint8_t*)p->ws_own;
+    return HP_OK;
+}
+
+DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_t* out,
+                   int64_t out_pitch, int64_t nout) {
+    DedispJob J;
+    J.xt = xt;
+    J.xt_pitch = xt_pitch;
+    J.out = out;
+    J.out_pitch = out_pitch;
+    J.nout = nout;
+    J.ntt = (int32_t)ceil_div(nout, p->tiling.BT);
+    J.ndt = (int32_t)p->tiling.tiles.size();
+    J.tiles = p->d_tiles;
+    J.stages = p->d_stages;
+    J.chans = p->d_chans;
+    J.addr = p->d_addr;
+    return J;
+}
+
+int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, uint8_t* xt, int64_t xt_pitch,
+               int32_t* out, int64_t out_pitch, cudaStream_t s) {
+    const int64_t nout = nsamps - p->maxd;
+    int ti = stage_begin(p, HP_STAGE_TRANSPOSE, s);
+    int rc = check_cuda(launch_transpose(fb, nsamps, p->nchans, xt, xt_pitch, s));
+    stage_end(p, HP_STAGE_TRANSPOSE, ti, s);
+    if (rc) return rc;
+    ++p->launches;
+    DedispBatch B;   // copied into the kernel parameters at launch
+    std::memset(&B, 0, sizeof(B));
+    B.njobs = 1;
+    B.jobs[0] = make_job(p, xt, xt_pitch, out, out_pitch, nout);
+    B.prefix[0] = 0;
+    B.prefix[1] = (int64_t)B.jobs[0].ntt * B.jobs[0].ndt;
+    ti = stage_begin(p, HP_STAGE_DEDISP, s);
+    rc = check_cuda(launch_dedisp(p->dedisp_cfg, B, p->status, p->timeout_ns, s));
+    stage_end(p, HP_STAGE_DEDISP, ti, s);
+    if (!rc) ++p->launches;
+    return rc;
+}
+
+int validate_search_input(const hp_plan* p, const void* ptr, int64_t nsamps) {
+    if (!p || !ptr) return HP_ERR_INVALID_ARG;
+    if (nsamps <= 0 || nsamps >= kMaxSamples) return HP_ERR_INVALID_ARG;
+    if (nsamps <= (int64_t)p->maxd + p->wmax) return HP_ERR_NSAMPS_TOO_SHORT;
+    return HP_OK;
+}
+
+SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int32_t* D,
+                            int64_t pitch, int64_t nout, hp_raw_cand* raw, int64_t raw_cap,
+                            int64_t* raw_count) {
+    SearchArgs a;
+    a.D = D;
+    a.pitch = pitch;
+    a.nout = nout;
+    a.ndm = p->ndm();
+    a.nw = p->nw();
+    a.widths = p->d_widths;
+    a.wmax = p->wmax;
+    a.thr = p->thr;
+    a.baseline_mode = p->baseline_mode;
+    a.win = baseline_window(p);
+    a.levels = remedian_levels(a.win);
+    a.lvl_a = (int32_t*)(ws + L.lvl_a);
+    a.lvl_b = (int32_t*)(ws + L.lvl_b);
+    a.lvl_pitch_a = L.lvl_pitch_a;
+    a.lvl_pitch_b = L.lvl_pitch_b;
+    a.mean_pre = (int64_t*)(ws + L.mean);
+    a.mean_pitch = L.mean_pitch;
+    a.hist = (uint32_t*)(ws + L.hist);
+    a.refine_bucket = (int32_t*)(ws + L.rbucket);
+    a.refine_rank = (int64_t*)(ws + L.rrank);
+    a.mad = (int64_t*)(ws + L.mad);
+    a.sigma = (double*)(ws + L.sigma);
+    a.tint = (int64_t*)(ws + L.tint);
+    a.raw = raw;
+    a.raw_cap = raw_cap;
+    a.raw_count = raw_count;
+    a.status = p->status;
+    return a;
+}
+
+MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw_cand* raw,
+                          const int64_t* nraw, int64_t cap, const double* sigma,
+                          hp_cand_buf* out) {
+    MergeArgs m;
+    m.raw = raw;
+    m.nraw = nraw;
+    m.cap = cap;
+    m.sigma = sigma;
+    m.widths = p->d_widths;
+    m.nw = p->nw();
+    m.wmax = p->wmax;
+    m.dm_tol = p->dm_tol;
+    m.t_gap = p->t_gap;
+    m.w_tol = p->w_tol;
+    m.keys[0] = (uint64_t*)(ws + L.keys0);
+    m.keys[1] = (uint64_t*)(ws + L.keys1);
+    m.vals[0] = (int64_t*)(ws + L.vals0);
+    m.vals[1] = (int64_t*)(ws + L.vals1);
+    m.parent = (int32_t*)(ws + L.parent);
+    m.best_bits = (uint64_t*)(ws + L.best);
+    m.rep = (int32_t*)(ws + L.rep);
+    m.members = (int32_t*)(ws + L.members);
+    m.dm_lo = (int32_t*)(ws + L.dmlo);
+    m.dm_hi = (int32_t*)(ws + L.dmhi);
+    m.t_lo = (unsigned long long*)(ws + L.tlo);
+    m.t_hi = (unsigned long long*)(ws + L.thi);
+    m.scan = (int32_t*)(ws + L.scan);
+    m.block_sums = (int32_t*)(ws + L.bsums);
+    m.n_clamped = (int64_t*)(ws + L.nclamp);
+    m.out = out->data;
+    m.out_cap = out->capacity;
+    m.out_count = out->count;
+    m.status = p->status;
+    return m;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* hp_status_str(int status) {
+    switch (status) {
+        case HP_OK: return "HP_OK";
+        case HP_ERR_INVALID_ARG: return "HP_ERR_INVALID_ARG";
+        case HP_ERR_CUDA: return "HP_ERR_CUDA";
+        case HP_ERR_OOM: return "HP_ERR_OOM";
+        case HP_ERR_CAND_OVERFLOW: return "HP_ERR_CAND_OVERFLOW";
+        case HP_ERR_TIMEOUT: return "HP_ERR_TIMEOUT";
+        case HP_ERR_NSAMPS_TOO_SHORT: return "HP_ERR_NSAMPS_TOO_SHORT";
+        default: return "HP_ERR_UNKNOWN";
+    }
+}
+
+int hp_plan_create(hp_plan** out, int nchans, double f_top_MHz, double chan_bw_MHz,
+                   double tsamp_s, const float* dm_list, int ndm, const int* boxcar_widths,
+                   int nw, float snr_threshold) {
+    if (!out) return HP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nchans < 1 || nchans > kMaxChans) return HP_ERR_INVALID_ARG;
+    if (!std::isfinite(f_top_MHz) || !(f_top_MHz > 0.0)) return HP_ERR_INVALID_ARG;
+    if (!std::isfinite(chan_bw_MHz) || !(chan_bw_MHz < 0.0)) return HP_ERR_INVALID_ARG;
+    if (!(f_top_MHz + (double)(nchans - 1) * chan_bw_MHz > 0.0)) return HP_ERR_INVALID_ARG;
+    if (!std::isfinite(tsamp_s) || !(tsamp_s > 0.0)) return HP_ERR_INVALID_ARG;
+    if (!dm_list || ndm < 1 || ndm > kMaxDMs) return HP_ERR_INVALID_ARG;
+    if (!boxcar_widths || nw < 1 || nw > kMaxWidths) return HP_ERR_INVALID_ARG;
+    if (!std::isfinite(snr_threshold) || !(snr_threshold > 0.0f)) return HP_ERR_INVALID_ARG;
+    for (int d = 0; d < ndm; ++d) {
+        if (!std::isfinite(dm_list[d]) || dm_list[d] < 0.0f) return HP_ERR_INVALID_ARG;
+        if (d > 0 && dm_list[d] < dm_list[d - 1]) return HP_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < nw; ++k) {
+        if (boxcar_widths[k] < 1 || boxcar_widths[k] > kMaxWidth) return HP_ERR_INVALID_ARG;
+        if (k > 0 && boxcar_widths[k] <= boxcar_widths[k - 1]) return HP_ERR_INVALID_ARG;
+    }
+    hp_plan* p = new (std::nothrow) hp_plan;
+    if (!p) return HP_ERR_OOM;
+    p->nchans = nchans;
+    p->f_top = f_top_MHz;
+    p->chan_bw = chan_bw_MHz;
+    p->tsamp = tsamp_s;
+    p->dm_list.assign(dm_list, dm_list + ndm);
+    p->widths.assign(boxcar_widths, boxcar_widths + nw);
+    p->thr = snr_threshold;
+    p->w_tol = nw;
+    p->wmax = boxcar_widths[nw - 1];
+    compute_delays(p);
+    // the sum of nchans bytes must fit int32 and every delay must be reachable
+    if ((int64_t)nchans * 255 > INT32_MAX || p->maxd >= kMaxSamples) {
+        delete p;
+        return HP_ERR_INVALID_ARG;
+    }
+    *out = p;
+    return HP_OK;
+}
+
+int hp_plan_destroy(hp_plan* p) {
+    if (!p) return HP_OK;
+    bool any_ev = false;
+    for (int st = 0; st < HP_NUM_STAGES; ++st) any_ev = any_ev || !p->ev[st].empty();
+    if (p->tables || p->ws_own || any_ev) cudaDeviceSynchronize();
+    if (p->tables) cudaFree(p->tables);
+    if (p->ws_own) cudaFree(p->ws_own);
+    for (int st = 0; st < HP_NUM_STAGES; ++st)
+        for (cudaEvent_t e : p->ev[st]) cudaEventDestroy(e);
+    delete p;
+    return HP_OK;
+}
+
+int hp_plan_set_param(hp_plan* p, int param, double v) {
+    if (!p || !std::isfinite(v)) return HP_ERR_INVALID_ARG;
+    switch (param) {
+        case HP_PARAM_BASELINE_MODE:
+            if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
+            p->baseline_mode = (int)v;
+            return HP_OK;
+        case HP_PARAM_BASELINE_S:
+            if (!(v > 0.0)) return HP_ERR_INVALID_ARG;
+            p->baseline_s = v;
+            return HP_OK;
+        case HP_PARAM_DM_TOL:
+            if (v < 0 || v > kMaxDMs || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->dm_tol = (int)v;
+            return HP_OK;
+        case HP_PARAM_T_GAP:
+            if (std::fabs(v) > 1e15 || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->t_gap = (int64_t)v;
+            return HP_OK;
+        case HP_PARAM_W_TOL:
+            if (v < 0 || v > kMaxWidths || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->w_tol = (int)v;
+            return HP_OK;
+        case HP_PARAM_RAW_CAPACITY:
+            if (v < 1024 || v > (double)((int64_t)1 << 30) || v != std::floor(v))
+                return HP_ERR_INVALID_ARG;
+            p->raw_capacity = (int64_t)v;
+            return HP_OK;
+        case HP_PARAM_DEDISP_CONFIG:
+            if (v < 0 || v >= kNumDedispConfigs || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->dedisp_cfg = (int)v;
+            return HP_OK;
+        case HP_PARAM_STAGE_TIMING:
+            if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
+            p->timing = v != 0.0;
+            return HP_OK;
+        case HP_PARAM_TIMEOUT_S:
+            if (!(v > 0.0) || v > 3600.0) return HP_ERR_INVALID_ARG;
+            p->timeout_ns = (uint64_t)(v * 1e9);
+            return HP_OK;
+        default:
+            return HP_ERR_INVALID_ARG;
+    }
+}
+
+int hp_plan_get_param(const hp_plan* p, int param, double* v) {
+    if (!p || !v) return HP_ERR_INVALID_ARG;
+    switch (param) {
+        case HP_PARAM_BASELINE_MODE: *v = p->baseline_mode; return HP_OK;
+        case HP_PARAM_BASELINE_S: *v = p->baseline_s; return HP_OK;
+        case HP_PARAM_DM_TOL: *v = p->dm_tol; return HP_OK;
+        case HP_PARAM_T_GAP: *v = (double)p->t_gap; return HP_OK;
+        case HP_PARAM_W_TOL: *v = p->w_tol; return HP_OK;
+        case HP_PARAM_RAW_CAPACITY: *v = (double)p->raw_capacity; return HP_OK;
+        case HP_PARAM_DEDISP_CONFIG: *v = p->dedisp_cfg; return HP_OK;
+        case HP_PARAM_STAGE_TIMING: *v = p->timing ? 1.0 : 0.0; return HP_OK;
+        case HP_PARAM_TIMEOUT_S: *v = (double)p->timeout_ns * 1e-9; return HP_OK;
+        default: return HP_ERR_INVALID_ARG;
+    }
+}
+
+int hp_plan_delays(const hp_plan* p, int32_t* out_host) {
+    if (!p || !out_host) return HP_ERR_INVALID_ARG;
+    std::memcpy(out_host, p->delays.data(), p->delays.size() * sizeof(int32_t));
+    return HP_OK;
+}
+
+int hp_plan_max_delay(const hp_plan* p, int32_t* max_delay) {
+    if (!p || !max_delay) return HP_ERR_INVALID_ARG;
+    *max_delay = p->maxd;
+    return HP_OK;
+}
+
+int hp_plan_workspace_bytes(const hp_plan* p, int64_t nsamps, size_t* bytes) {
+    if (!p || !bytes) return HP_ERR_INVALID_ARG;
+    if (nsamps <= (int64_t)p->maxd + p->wmax) return HP_ERR_NSAMPS_TOO_SHORT;
+    *bytes = make_layout(p, nsamps, true).total;
+    return HP_OK;
+}
+
+int hp_plan_bind_workspace(hp_plan* p, void* ws, size_t bytes) {
+    if (!p) return HP_ERR_INVALID_ARG;
+    if (ws && ((uintptr_t)ws & 255u)) return HP_ERR_INVALID_ARG;
+    p->ws_user = ws;
+    p->ws_user_bytes = ws ? bytes : 0;
+    return HP_OK;
+}
+
+int hp_dedisperse(hp_plan* p, const uint8_t* fb, int64_t nsamps, int32_t* out, int64_t pitch,
+                  void* stream) {
+    int rc = validate_search_input(p, fb, nsamps);
+    if (rc) return rc;
+    const int64_t nout = nsamps - p->maxd;
+    if (!out || pitch < nout || (pitch & 3) || ((uintptr_t)out & 15u)) return HP_ERR_INVALID_ARG;
+    rc = ensure_device_tables(p);
+    if (rc) return rc;
+    Layout L = make_layout(p, nsamps, true);
+    uint8_t* ws = nullptr;
+    rc = ensure_workspace(p, L.total, &ws);
+    if (rc) return rc;
+    return run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, out, pitch, (cudaStream_t)stream);
+}
+
+int hp_detect(hp_plan* p, const int32_t* series, int64_t nout, int64_t pitch, void* stream,
+              hp_raw_buf* raw_out, double* sigma_dev, int64_t* mad_dev) {
+    if (!p || !series || !raw_out || !raw_out->data || !raw_out->count || raw_out->capacity < 0)
+        return HP_ERR_INVALID_ARG;
+    if (nout <= p->wmax || pitch < nout) return HP_ERR_NSAMPS_TOO_SHORT;
+    int rc = ensure_device_tables(p);
+    if (rc) return rc;
+    Layout L = make_layout(p, nout + p->maxd, false);
+    uint8_t* ws = nullptr;
+    rc = ensure_workspace(p, L.total, &ws);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    SearchArgs a = make_search_args(p, L, ws, series, pitch, nout, raw_out->data,
+                                    raw_out->capacity, raw_out->count);
+    const int ti = stage_begin(p, HP_STAGE_SEARCH, s);
+    rc = check_cuda(launch_search(a, s, &p->launches));
+    stage_end(p, HP_STAGE_SEARCH, ti, s);
+    if (rc) return rc;
+    if (sigma_dev)
+        rc = check_cuda(cudaMemcpyAsync(sigma_dev, a.sigma, sizeof(double) * p->ndm(),
+                                        cudaMemcpyDeviceToDevice, s));
+    if (!rc && mad_dev)
+        rc = check_cuda(cudaMemcpyAsync(mad_dev, a.mad, sizeof(int64_t) * p->ndm(),
+                                        cudaMemcpyDeviceToDevice, s));
+    return rc;
+}
+
+int hp_merge(hp_plan* p, const hp_raw_cand* raw, const int64_t* nraw, int64_t raw_capacity,
+             const double* sigma, void* stream, hp_cand_buf* out) {
+    if (!p || !raw || !nraw || !sigma || !out || !out->data || !out->count || out->capacity < 0 ||
+        raw_capacity < 0)
+        return HP_ERR_INVALID_ARG;
+    int rc = ensure_device_tables(p);
+    if (rc) return rc;
+    // the merge scratch is sized by the plan's raw capacity
+    if (raw_capacity > p->raw_capacity) return HP_ERR_INVALID_ARG;
+    Layout L = make_layout(p, (int64_t)p->maxd + p->wmax + 1, false);
+    uint8_t* ws = nullptr;
+    rc = ensure_workspace(p, L.total, &ws);
+    if (rc) return rc;
+    MergeArgs m = make_merge_args(p, L, ws, raw, nraw, raw_capacity, sigma, out);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ti = stage_begin(p, HP_STAGE_MERGE, s);
+    rc = check_cuda(launch_merge(m, s, &p->launches));
+    stage_end(p, HP_STAGE_MERGE, ti, s);
+    return rc;
+}
+
+int hp_search(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream, hp_cand_buf* out) {
+    int rc = validate_search_input(p, fb, nsamps);
+    if (rc) return rc;
+    if (!out || !out->data || !out->count || out->capacity < 0) return HP_ERR_INVALID_ARG;
+    rc = ensure_device_tables(p);
+    if (rc) return rc;
+    Layout L = make_layout(p, nsamps, true);
+    uint8_t* ws = nullptr;
+    rc = ensure_workspace(p, L.total, &ws);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* D = (int32_t*)(ws + L.D);
+    rc = run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, D, L.dpitch, s);
+    if (rc) return rc;
+    hp_raw_cand* raw = (hp_raw_cand*)(ws + L.raw);
+    int64_t* raw_count = (int64_t*)(ws + L.raw_count);
+    SearchArgs a = make_search_args(p, L, ws, D, L.dpitch, L.nout, raw, p->raw_capacity, raw_count);
+    int ti = stage_begin(p, HP_STAGE_SEARCH, s);
+    rc = check_cuda(launch_search(a, s, &p->launches));
+    stage_end(p, HP_STAGE_SEARCH, ti, s);
+    if (rc) return rc;
+    MergeArgs m = make_merge_args(p, L, ws, raw, raw_count, p->raw_capacity, a.sigma, out);
+    ti = stage_begin(p, HP_STAGE_MERGE, s);
+    rc = check_cuda(launch_merge(m, s, &p->launches));
+    stage_end(p, HP_STAGE_MERGE, ti, s);
+    return rc;
+}
+
+int hp_plan_stats(hp_plan* p, hp_stats* out, int reset) {
+    if (!p || !out) return HP_ERR_INVALID_ARG;
+    for (int st = 0; st < HP_NUM_STAGES; ++st) {
+        double ms = 0.0;
+        for (int i = 0; i < p->ev_used[st]; ++i) {
+            if (cudaEventSynchronize(p->ev[st][2 * i + 1]) != cudaSuccess) return HP_ERR_CUDA;
+            float f = 0.f;
+            if (cudaEventElapsedTime(&f, p->ev[st][2 * i], p->ev[st][2 * i + 1]) != cudaSuccess)
+                return HP_ERR_CUDA;
+            ms += f;
+        }
+        out->stage_ms[st] = ms;
+        out->stage_calls[st] = p->ev_used[st];
+        if (reset) p->ev_used[st] = 0;
+    }
+    out->kernel_launches = p->launches;
+    if (reset) p->launches = 0;
+    return HP_OK;
+}
+
+int hp_plan_sync_status(hp_plan* p, void* stream) {
+    if (!p) return HP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HP_ERR_CUDA;
+    if (!p->status) return HP_OK;
+    int st = 0;
+    if (cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HP_ERR_CUDA;
+    if (st != 0 && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return HP_ERR_CUDA;
+    return st;
+}
+
+}  // extern "C"

@@ -67,6 +67,7 @@ class Pulse:
     t0: float
     fwhm: float
     amp: float
+    snr: float = float("nan")   # nominal best-boxcar S/N the amplitude was derived from
 
 
 @dataclass(frozen=True)

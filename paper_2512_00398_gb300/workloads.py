@@ -68,7 +68,7 @@ def _random_pulses(obs, rng, n, dm_hi, fwhm_lo, fwhm_hi, snr_lo, snr_hi, t_hi):
         snr = float(rng.uniform(snr_lo, snr_hi))
         t0 = float(rng.uniform(0.05 * t_hi, 0.95 * t_hi))
         amp = synth.amp_for_matched_snr(snr, fwhm / obs.tsamp, obs.nchans, obs.sigma)
-        out.append(synth.Pulse(dm, t0, fwhm, amp))
+        out.append(synth.Pulse(dm, t0, fwhm, amp, snr))
     return out
 
 

@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every symbol include/hp.h declares, validates arguments, and its FP64 delay
+table is bit-identical to the oracle's (computed independently)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2512_00398_gb300 as hp
+from paper_2512_00398_gb300 import synth, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(hp_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hp.lib()
+    declared = _declared()
+    assert "hp_search" in declared and "hp_plan_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(hp.EXPORTS) >= declared
+
+
+def test_status_strings():
+    assert hp.status_str(0) == "HP_OK"
+    assert hp.status_str(-6) == "HP_ERR_NSAMPS_TOO_SHORT"
+    assert hp.status_str(12345) == "HP_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("make", [workloads.tiny, lambda: workloads.fast(nsamps=1 << 17),
+                                  lambda: workloads.stress(nsamps=1 << 18)])
+def test_delay_table_matches_oracle(make):
+    w = make()
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold) as p:
+        assert np.array_equal(p.delays(), oracle.delays(o.nchans, o.f_top, o.chan_bw, o.tsamp,
+                                                        w.dm_list))
+        assert p.max_delay == int(p.delays().max())
+
+
+def test_delay_table_matches_oracle_batch_files():
+    for w in workloads.batch(nfiles=4):
+        o = w.obs
+        with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
+            assert np.array_equal(p.delays(), oracle.delays(o.nchans, o.f_top, o.chan_bw,
+                                                            o.tsamp, w.dm_list))
+
+
+BAD = [
+    dict(nchans=0), dict(nchans=70000), dict(f_top=-1.0), dict(chan_bw=0.0), dict(chan_bw=1.0),
+    dict(chan_bw=-30.0), dict(tsamp=0.0), dict(tsamp=float("nan")), dict(dm_list=[]),
+    dict(dm_list=[5.0, 1.0]), dict(dm_list=[-1.0]), dict(dm_list=[float("inf")]), dict(widths=[]),
+    dict(widths=[2, 2]), dict(widths=[0, 1]), dict(widths=list(range(1, 40))), dict(widths=[1, 32768]),
+    dict(thr=0.0), dict(thr=float("nan")),
+]
+
+
+@pytest.mark.parametrize("bad", BAD)
+def test_plan_rejects_bad_arguments(bad):
+    args = dict(nchans=64, f_top=1500.0, chan_bw=-2.0, tsamp=1e-4, dm_list=[0.0, 10.0],
+                widths=[1, 2, 4], thr=6.0)
+    args.update(bad)
+    with pytest.raises(hp.HPError) as e:
+        hp.Plan(args["nchans"], args["f_top"], args["chan_bw"], args["tsamp"], args["dm_list"],
+                args["widths"], args["thr"])
+    assert e.value.code == hp.HP_ERR_INVALID_ARG
+
+
+def test_params_roundtrip_and_validation():
+    w = workloads.tiny()
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
+        assert p.get_param("w_tol") == w.nw
+        for name, val in [("baseline_mode", 1), ("baseline_s", 0.5), ("dm_tol", 3), ("t_gap", -2),
+                          ("w_tol", 1), ("raw_capacity", 4096), ("dedisp_config", 3),
+                          ("stage_timing", 1), ("timeout_s", 0.25)]:
+            p.set_param(name, val)
+            assert p.get_param(name) == pytest.approx(val)
+        for name, val in [("baseline_mode", 2), ("baseline_s", 0), ("dm_tol", -1), ("w_tol", 0.5),
+                          ("raw_capacity", 10), ("dedisp_config", hp.HP_NUM_DEDISP_CONFIGS),
+                          ("timeout_s", 0)]:
+            with pytest.raises(hp.HPError):
+                p.set_param(name, val)
+        with pytest.raises(hp.HPError):
+            p.set_param(99, 1.0)
+
+
+def test_workspace_sizes():
+    w = workloads.fast(nsamps=1 << 20)
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
+        nout = p.nout(1 << 20)
+        ws = p.workspace_bytes(1 << 20)
+        assert ws >= o.nchans * (1 << 20) + 4 * w.ndm * nout        # transposed input + series
+        assert ws < 12e9
+        with pytest.raises(hp.HPError) as e:
+            p.workspace_bytes(p.max_delay + int(w.widths[-1]))
+        assert e.value.code == hp.HP_ERR_NSAMPS_TOO_SHORT
