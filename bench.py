@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 single-pulse search (one JSON line on rank 0).
+
+A step is one whole search (dedispersion, per-trial baseline / sigma /
+boxcars / peaks, merge) of one synthetic filterbank shaped like the paper's
+single-file FAST workload: 4096 channels over 1000-1500 MHz, 2^20 samples of
+49.152 us (51.5 s), ~1500 trials on DM 0-2000, boxcars 1..4096, S/N 6.
+The 4.3 GB input is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank searches its own file
+(weak scaling, no collective on the data path); the time is the max over ranks.
+``--impl reference`` times the CPU oracle on the host cores instead, on a
+bounded sample of trials of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DM-trial·samples/s"
+
+# DRAM traffic of the dedispersion kernel from the last ncu capture
+# (profiles/dedisp_kernel_fast_4096ch.md): read + write bytes per launch divided by
+# the output samples per trial of the captured case (the traffic grows with the
+# number of time tiles).  Keyed by the kernel source it was measured on; a changed
+# kernel reports null until it is captured again.
+DEDISP_TRAFFIC = {"source_sha256_16": "83dd9a408eae2429", "bytes_per_output_sample": 7.330154e9 / 37556,
+                  "ndm": 1500, "nchans": 4096}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dedisp-config", type=int, default=None)
+    ap.add_argument("--nsamps", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of one GPU during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload
+def workload(nsamps):
+    from paper_2512_00398_gb300 import workloads
+    return workloads.fast(nsamps=nsamps)
+
+
+def describe(w, nout):
+    o = w.obs
+    return {"workload": f"single FAST-like filterbank: {o.nchans} ch x {o.nsamps} samples "
+                        f"({o.duration:.1f} s at {o.tsamp * 1e6:.3f} us), {w.ndm} trials on "
+                        f"DM 0-{float(w.dm_list[-1]):.0f}, boxcars 1..{int(w.widths[-1])}, S/N "
+                        f"{w.threshold:g}, 20 injected pulses",
+            "nchans": o.nchans, "nsamps": o.nsamps, "tsamp_s": o.tsamp, "ndm": w.ndm,
+            "nout": nout, "nw": w.nw, "l2": "inputs larger than L2 (no flush)"}
+
+
+def dedisp_traffic(w, nout):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2512_00398_gb300", "csrc", "dedisp.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    t = DEDISP_TRAFFIC
+    if sha != t["source_sha256_16"] or w.ndm != t["ndm"] or w.obs.nchans != t["nchans"]:
+        return None
+    return t["bytes_per_output_sample"] * nout
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(s, w, ntrials, d0=None):
+    """Time the oracle on `ntrials` consecutive trials of the full input."""
+    import oracle
+    o = w.obs
+    tab = oracle.delays(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list)
+    nout = o.nsamps - int(tab.max())
+    if d0 is None:
+        d0 = max(0, w.ndm // 2 - ntrials // 2)
+    t = time.perf_counter()
+    D = oracle.dedisperse(s.data, tab, rows=(d0, d0 + ntrials), nout=nout)
+    raw, _, _ = oracle.search_trials(D, d0, o.tsamp, w.widths, w.threshold)
+    oracle.merge(raw, w.widths)
+    dt = time.perf_counter() - t
+    return dt, ntrials * nout, nout
+
+
+def cpu_baseline(s, w, budget_s=15.0):
+    import oracle
+    dt1, units1, nout = oracle_sample(s, w, 1)
+    k = int(max(1, min(64, budget_s / max(dt1, 1e-3))))
+    dt, units, _ = oracle_sample(s, w, k)
+    return {"value": units / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{k} consecutive trials (of {w.ndm}) around the middle of the DM range, "
+                      f"full {w.obs.nsamps} samples: dedispersion + per-trial stages + merge, "
+                      f"{dt:.1f} s"}
+
+
+# -------------------------------------------------------------- our path
+def run_ours(args):
+    import torch
+    import paper_2512_00398_gb300 as hp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = workload(args.nsamps)
+    if world > 1:   # weak scaling: every rank its own file
+        from paper_2512_00398_gb300 import workloads
+        w = workloads.fast(nsamps=args.nsamps, seed=2 + rank)
+    s = w.generate(threads=min(16, os.cpu_count() or 8))
+    o = w.obs
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    if args.dedisp_config is not None:
+        plan.set_param("dedisp_config", args.dedisp_config)
+    nout = plan.nout(o.nsamps)
+    plan.bind_workspace(o.nsamps)
+    fb = torch.from_numpy(s.data).cuda()
+    out = hp.new_cand_buf(1 << 16)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        hp.hp_search(plan, fb, stream, out=out)
+    st = hp.hp_plan_sync_status(plan, stream)
+    if st != hp.HP_OK:
+        raise hp.HPError(st, "warm-up")
+    ncl = int(out[1].item())
+    hp.hp_plan_stats(plan, reset=True)
+    plan.set_param("stage_timing", 1)
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            hp.hp_search(plan, fb, stream, out=out)
+        e1.record(stream)
+        barrier()
+    dev_ms = e0.elapsed_time(e1) / args.steps
+    st = hp.hp_plan_sync_status(plan, stream)
+    if st != hp.HP_OK:
+        raise hp.HPError(st, "timed region")
+    stats = hp.hp_plan_stats(plan, reset=True)
+    plan.set_param("stage_timing", 0)
+
+    # end to end through the public call: pinned host input -> device, search,
+    # device -> host read of the count and the candidate records
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(s.data).pin_memory()
+        res = torch.empty(out[0].numel(), dtype=torch.uint8).pin_memory()
+        cnt_h = torch.empty(1, dtype=torch.int64).pin_memory()
+        d2h = []
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                barrier()
+                t0 = time.perf_counter()
+            fb.copy_(host, non_blocking=True)
+            hp.hp_search(plan, fb, stream, out=out)
+            cnt_h.copy_(out[1], non_blocking=True)
+            stream.synchronize()
+            n = min(int(cnt_h.item()), out[0].numel() // hp.CAND_DTYPE.itemsize)
+            nb = n * hp.CAND_DTYPE.itemsize
+            if nb:
+                res[:nb].copy_(out[0][:nb], non_blocking=True)
+            stream.synchronize()
+            if it >= args.warmup:
+                d2h.append(8 + nb)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = [e2e_s, float(np.mean(d2h))]
+
+    # max over ranks
+    vals = torch.tensor([dev_ms, e2e[0] if e2e else 0.0], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    dev_ms, e2e_s = float(vals[0]), float(vals[1])
+    units = w.ndm * nout
+    line = None
+    if rank == 0:
+        value = world * units / (dev_ms * 1e-3)
+        clocks = clk.summary()
+        adds = float(w.ndm) * o.nchans * nout
+        dd_ms = stats["stage_ms"]["dedisp"] / max(1, stats["stage_calls"]["dedisp"])
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded noise + dispersed pulses, shaped like a FAST file)",
+            "config": describe(w, nout),
+            "rtf": world * o.duration / (dev_ms * 1e-3),
+            "clusters": ncl,
+            "stages_ms": {k: v / max(1, stats["stage_calls"][k])
+                          for k, v in stats["stage_ms"].items()},
+            "gpu_launches": stats["kernel_launches"],
+        }
+        peaks = hp.hp_measure_peaks()
+        sm_mhz = clocks["sm_mhz"] or 0.0
+        # ALU roofline: 16-bit x 2 SWAR lanes give two byte-adds per 32-bit lane
+        # operation, so the add peak is twice the measured 32-bit add issue rate
+        peak_adds = 2.0 * peaks["int_add_ops_per_s"]
+        achieved = adds / (dd_ms * 1e-3)
+        line["roofline"] = {
+            "bound": "alu", "kernel": "dedisp_kernel", "achieved": achieved / 1e12,
+            "peak": peak_adds / 1e12, "unit": "Tadd/s", "frac": achieved / peak_adds,
+            "traffic": dedisp_traffic(w, nout),
+            "algorithmic": f"{w.ndm} trials x {o.nchans} ch x {nout} samples = {adds:.3e} "
+                           f"byte-adds per launch",
+            "peak_basis": "measured int32 add issue rate x 2 (16-bit SWAR lanes); "
+                          f"int32 {peaks['int_add_ops_per_s'] / 1e12:.2f} Tops/s, PRMT "
+                          f"{peaks['prmt_ops_per_s'] / 1e12:.2f} Tops/s, LDS.32 "
+                          f"{peaks['lds32_bytes_per_s'] / 1e12:.2f} TB/s, "
+                          f"{peaks['sm_count']} SMs",
+            "frac_vs_int32_rate": achieved / peaks["int_add_ops_per_s"],
+        }
+        line["clocks"] = clocks
+        if e2e:
+            line["e2e"] = {"value": world * units / e2e_s, "unit": METRIC,
+                           "h2d_bytes_per_step": int(s.data.nbytes), "d2h_bytes_per_step": int(e2e[1]),
+                           "ms_per_step": e2e_s * 1e3}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(s, w)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    w = workload(args.nsamps)
+    s = w.generate(threads=min(16, os.cpu_count() or 8))
+    dt1, _, nout = oracle_sample(s, w, 1)
+    k = int(max(1, min(64, 8.0 / max(dt1, 1e-3))))
+    for i in range(args.warmup):
+        oracle_sample(s, w, k, d0=(i * k) % max(1, w.ndm - k))
+    times = []
+    for i in range(args.steps):
+        dt, units, _ = oracle_sample(s, w, k, d0=((args.warmup + i) * k) % max(1, w.ndm - k))
+        times.append(dt)
+    step = float(np.mean(times))
+    value = k * nout / step
+    sample = (f"{k} consecutive trials (of {w.ndm}) per step, full {w.obs.nsamps} samples: "
+              f"dedispersion + per-trial stages + merge")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": describe(w, nout),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,33 @@
+/*
+ * hp_bench.h -- measurement helpers of the search library (no counterpart in
+ * the paper).  They measure the issue rates that bound the dedispersion
+ * kernel, which is limited by integer-ALU and shared-memory throughput, not by
+ * HBM bandwidth or tensor cores.
+ */
+#ifndef HP_BENCH_H
+#define HP_BENCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double int_add_ops_per_s;   /* 32-bit integer adds (lane operations) per second */
+    double prmt_ops_per_s;      /* byte-permute lane operations per second */
+    double lds32_bytes_per_s;   /* conflict-free 32-bit shared-memory load bytes per second */
+    int sm_count;               /* multiprocessors of the current device */
+    int reserved;
+} hp_peaks;
+
+/* Run the microbenchmarks on the current device (synchronous, about a
+ * second).  Each kernel fills every SM with independent dependency chains,
+ * is timed with CUDA events after a warm-up launch, and the rate is the best
+ * of three launches.  *out is host memory.  Returns HP_OK or HP_ERR_CUDA. */
+int hp_measure_peaks(hp_peaks* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HP_BENCH_H */

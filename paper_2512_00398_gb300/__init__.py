@@ -19,7 +19,7 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_PARAM_DEDISP_CONFIG, HP_PARAM_DM_TOL, HP_PARAM_RAW_CAPACITY,
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
-                   STAGE_NAMES, CandBuf, HPError, Stats, check, lib, status_str)
+                   STAGE_NAMES, CandBuf, HPError, Peaks, Stats, check, lib, status_str)
 
 _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASELINE_S,
            "dm_tol": HP_PARAM_DM_TOL, "t_gap": HP_PARAM_T_GAP, "w_tol": HP_PARAM_W_TOL,
@@ -185,6 +185,8 @@ def hp_dedisperse(plan: Plan, filterbank, stream=None, out=None):
     torch = _torch()
     _check_fb(plan, filterbank)
     nout = plan.nout(filterbank.shape[0])
+    if nout <= int(plan.widths[-1]):
+        raise HPError(HP_ERR_NSAMPS_TOO_SHORT, "hp_dedisperse")
     if out is None:
         pitch = (nout + 3) // 4 * 4
         out = torch.empty((plan.ndm, pitch), dtype=torch.int32, device=filterbank.device)
@@ -233,6 +235,14 @@ def hp_plan_stats(plan: Plan, reset: bool = True) -> dict:
     return {"stage_ms": {n: st.stage_ms[i] for i, n in enumerate(STAGE_NAMES)},
             "stage_calls": {n: int(st.stage_calls[i]) for i, n in enumerate(STAGE_NAMES)},
             "kernel_launches": int(st.kernel_launches)}
+
+
+def hp_measure_peaks() -> dict:
+    """Integer-add, byte-permute and shared-memory load rates of the current GPU."""
+    pk = Peaks()
+    check(lib().hp_measure_peaks(C.byref(pk)), "hp_measure_peaks")
+    return {"int_add_ops_per_s": pk.int_add_ops_per_s, "prmt_ops_per_s": pk.prmt_ops_per_s,
+            "lds32_bytes_per_s": pk.lds32_bytes_per_s, "sm_count": int(pk.sm_count)}
 
 
 # ------------------------------------------------------- host conveniences

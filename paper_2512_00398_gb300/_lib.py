@@ -49,7 +49,7 @@ assert CAND_DTYPE.itemsize == 48 and RAW_DTYPE.itemsize == 24
 EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_param",
            "hp_plan_get_param", "hp_plan_delays", "hp_plan_max_delay", "hp_plan_workspace_bytes",
            "hp_plan_bind_workspace", "hp_search", "hp_dedisperse", "hp_detect", "hp_merge",
-           "hp_plan_sync_status", "hp_plan_stats")
+           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks")
 
 
 class HPError(RuntimeError):
@@ -60,6 +60,11 @@ class HPError(RuntimeError):
 
 class CandBuf(C.Structure):
     _fields_ = [("data", C.c_void_p), ("capacity", C.c_int64), ("count", C.c_void_p)]
+
+
+class Peaks(C.Structure):
+    _fields_ = [("int_add_ops_per_s", C.c_double), ("prmt_ops_per_s", C.c_double),
+                ("lds32_bytes_per_s", C.c_double), ("sm_count", C.c_int), ("reserved", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -96,6 +101,7 @@ def lib() -> C.CDLL:
             L.hp_merge.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(CandBuf)]
             L.hp_plan_sync_status.argtypes = [vp, vp]
             L.hp_plan_stats.argtypes = [vp, C.POINTER(Stats), i32]
+            L.hp_measure_peaks.argtypes = [C.POINTER(Peaks)]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32

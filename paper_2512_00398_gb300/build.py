@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhp.so")
-SOURCES = ["plan.cpp", "dedisp.cu", "search.cu", "merge.cu"]
+SOURCES = ["plan.cpp", "dedisp.cu", "search.cu", "merge.cu", "peaks.cu"]
 HEADERS = ["common.cuh", "hp_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -30,6 +30,7 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     files.append(os.path.join(ROOT, "include", "hp.h"))
+    files.append(os.path.join(ROOT, "include", "hp_bench.h"))
     files.append(os.path.abspath(__file__))
     return files
 

@@ -81,7 +81,7 @@ def test_dedisp_bit_exact_ragged(hp, torch, cfg):
     from paper_2512_00398_gb300 import synth
     rng = np.random.default_rng(11)
     nch, nsamps = 100, 20011
-    dms = np.sort(np.concatenate([[0, 0, 3.5, 3.5], rng.uniform(0, 900, 37), [2500.0]]))
+    dms = np.sort(np.concatenate([[0, 0, 3.5, 3.5], rng.uniform(0, 900, 37), [1500.0]]))
     dms = dms.astype(np.float32)
     x = rng.integers(0, 256, size=(nsamps, nch), dtype=np.uint8)
     x[rng.integers(0, nsamps, 50)] = 255
@@ -236,7 +236,13 @@ def test_fast_full_size_sampled(hp, torch, fast_full):
     got = hp.search(p, fb)
     assert int(got["members"].sum()) == raw_g.size
     assert (got["dm_lo"] <= got["dm_idx"]).all() and (got["dm_idx"] <= got["dm_hi"]).all()
+    assert (got["t_lo"] <= got["sample"]).all() and (got["sample"] < got["t_hi"]).all()
+
+
+def test_fast_full_size_recovery(hp, torch, fast_full):
     from tests.test_oracle_pins import recovered
+    w, s, fb = fast_full
+    got = hp.search(_plan(hp, w), fb)
     bright = [pl for pl in s.pulses if pl.snr >= 10.0]
     missed = [pl for pl in bright if not recovered(pl, got, w, snr_min=w.threshold)]
     assert not missed, missed
