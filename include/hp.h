@@ -209,6 +209,33 @@ typedef struct {
  * into *out (host), then reset them if `reset` is non-zero. */
 int hp_plan_stats(hp_plan* plan, hp_stats* out, int reset);
 
+/* Candidate merging that allocates nothing (the paper has no counterpart).
+ * Some callers cannot allocate device memory when they merge: a real-time
+ * pipeline that forbids allocation after start-up (cudaMalloc can block and can
+ * fail on a full device), or code inside a framework that owns all device
+ * memory.  This call runs the same kernels as hp_merge, with the same result,
+ * but keeps all of their scratch in one fixed device array built into the
+ * library (about 5.3 MB, reserved on every GPU that loads the library until the
+ * process exits), and it calls no cudaMalloc, cudaFree or allocating library
+ * routine.  No plan is needed:
+ *   raw_dev / nraw_dev  device raw candidates and their device count
+ *   raw_capacity        entries of raw_dev, at most HP_MERGE_STATIC_MAX_RAW;
+ *                       larger values are rejected with HP_ERR_INVALID_ARG
+ *   sigma_dev           device double [ndm], per-trial sigma (as hp_detect writes)
+ *   boxcar_widths       host, nw strictly increasing widths (as in the plan)
+ *   dm_tol, t_gap, w_tol  merge tolerances (HP_PARAM_DM_TOL/T_GAP/W_TOL)
+ *   cand_out            merged clusters (see hp_cand_buf)
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array, and its contents persist
+ * from call to call (every word the kernels read is rewritten first, so nothing
+ * has to be cleared); calls whose work overlaps on the GPU, e.g. on two streams
+ * at once, race on it and must be ordered by the caller. */
+#define HP_MERGE_STATIC_MAX_RAW 65536
+int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_dev, int64_t raw_capacity,
+                    const double* sigma_dev, const int* boxcar_widths, int nw, int dm_tol,
+                    int64_t t_gap, int w_tol, void* stream, hp_cand_buf* cand_out);
+
 /* Wait for the plan's enqueued work on `stream` and return (then clear) the
  * first device-side status latched since the last call: HP_OK,
  * HP_ERR_CAND_OVERFLOW or HP_ERR_TIMEOUT.  Synchronises the stream. */

@@ -19,7 +19,8 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_PARAM_DEDISP_CONFIG, HP_PARAM_DM_TOL, HP_PARAM_RAW_CAPACITY,
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
-                   STAGE_NAMES, CandBuf, HPError, Peaks, Stats, check, lib, status_str)
+                   STAGE_NAMES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks, Stats, check, lib,
+                   status_str)
 
 _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASELINE_S,
            "dm_tol": HP_PARAM_DM_TOL, "t_gap": HP_PARAM_T_GAP, "w_tol": HP_PARAM_W_TOL,
@@ -221,6 +222,24 @@ def hp_merge(plan: Plan, raw, raw_count, sigma, stream=None, out=None, capacity:
     check(lib().hp_merge(plan.handle, C.c_void_p(raw.data_ptr()), C.c_void_p(raw_count.data_ptr()),
                          int(raw_cap), C.c_void_p(sigma.data_ptr()), _stream_ptr(stream),
                          C.byref(b)), "hp_merge")
+    return data, count
+
+
+def hp_merge_static(raw, raw_count, sigma, widths, dm_tol=1, t_gap=0, w_tol=None, stream=None,
+                    out=None, capacity: int = 1 << 16):
+    """Merge device raw candidates without any device allocation by the
+    library (its scratch is a fixed array built into the library); for
+    callers that must not allocate.  Returns the device (data, count) pair."""
+    data, count = out if out is not None else new_cand_buf(capacity, raw.device)
+    cap = data.numel() // CAND_DTYPE.itemsize
+    b = _buf(data, count, cap)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    raw_cap = raw.numel() // RAW_DTYPE.itemsize
+    check(lib().hp_merge_static(C.c_void_p(raw.data_ptr()), C.c_void_p(raw_count.data_ptr()),
+                                int(raw_cap), C.c_void_p(sigma.data_ptr()),
+                                w.ctypes.data_as(C.c_void_p), int(w.size), int(dm_tol), int(t_gap),
+                                int(w.size if w_tol is None else w_tol), _stream_ptr(stream),
+                                C.byref(b)), "hp_merge_static")
     return data, count
 
 

@@ -49,7 +49,10 @@ assert CAND_DTYPE.itemsize == 48 and RAW_DTYPE.itemsize == 24
 EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_param",
            "hp_plan_get_param", "hp_plan_delays", "hp_plan_max_delay", "hp_plan_workspace_bytes",
            "hp_plan_bind_workspace", "hp_search", "hp_dedisperse", "hp_detect", "hp_merge",
-           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks")
+           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks", "hp_merge_static")
+
+#: raw-candidate limit of hp_merge_static
+HP_MERGE_STATIC_MAX_RAW = 65536
 
 
 class HPError(RuntimeError):
@@ -102,6 +105,8 @@ def lib() -> C.CDLL:
             L.hp_plan_sync_status.argtypes = [vp, vp]
             L.hp_plan_stats.argtypes = [vp, C.POINTER(Stats), i32]
             L.hp_measure_peaks.argtypes = [C.POINTER(Peaks)]
+            L.hp_merge_static.argtypes = [vp, vp, i64, vp, vp, i32, i32, i64, i32, vp,
+                                          C.POINTER(CandBuf)]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32
