@@ -30,12 +30,14 @@ constexpr int64_t kMaxSamples = (int64_t)1 << 38;
 // ------------------------------------------------------ dedispersion tiles
 // Thread tile: RD trials x NW words (4 samples each) per thread; WD warps
 // along the trial axis, WT along time.  BD = WD*RD trials, BT = WT*NW*128
-// samples per block.
+// samples per block, 32*WD*WT threads.
+constexpr int kDedispStages = 3;         // shared-memory ring of channel stages
 struct DedispConfig {
     int RD, NW, WD, WT;
-    int stage_bytes;   // shared memory per pipeline stage (two stages per block)
+    int stage_bytes;   // shared memory per stage buffer (kDedispStages per block)
     int BD() const { return WD * RD; }
     int BT() const { return WT * NW * 128; }
+    int threads() const { return 32 * WD * WT; }
 };
 constexpr int kNumDedispConfigs = 4;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
@@ -49,11 +51,17 @@ struct ChanDesc {
 };
 static_assert(sizeof(ChanDesc) == 16, "ChanDesc layout");
 
+// One channel stage of a DM tile.  In the stage buffer: nchan channel
+// descriptors, then the address table [pair][BD][2] (uint32 byte offsets of
+// the first word each trial reads in each channel of a channel pair), then
+// the rows with their shifted copies.
 struct StageDesc {
     uint32_t chan_begin;  // index into the channel-descriptor array
     uint32_t nchan;
-    uint32_t addr_off;    // byte offset of the word-address table in the buffer
+    uint32_t addr_off;    // byte offset of the address table in the buffer
     uint32_t tx_bytes;    // bytes landing in shared memory for this stage
+    uint32_t addr_begin;  // index of the stage's table in the address array
+    uint32_t addr_bytes;  // table bytes (pairs * BD * 8)
 };
 
 struct TileDesc {
@@ -68,7 +76,7 @@ struct DedispTiling {
     std::vector<TileDesc> tiles;
     std::vector<StageDesc> stages;
     std::vector<ChanDesc> chans;
-    std::vector<uint16_t> addr;    // [chan desc][BD] word addresses in the stage buffer
+    std::vector<uint32_t> addr;    // per stage [pair][BD][2] byte offsets in the stage buffer
     int64_t max_reach = 0;         // max over rows of goff + row bytes
 };
 
@@ -84,7 +92,7 @@ struct DedispJob {
     const TileDesc* tiles;
     const StageDesc* stages;
     const ChanDesc* chans;
-    const uint16_t* addr;
+    const uint32_t* addr;
 };
 
 // Jobs of one dedispersion launch, passed by value as the kernel parameter.
@@ -104,6 +112,15 @@ cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8
                              int64_t xt_pitch, cudaStream_t s);
 cudaError_t launch_dedisp(int cfg, const DedispBatch& batch, int* status, uint64_t timeout_ns,
                           cudaStream_t s);
+
+// A run that left the detect tile's halo, to be finished by tail_kernel.
+struct TailRec {
+    int32_t trial, k;
+    int64_t u;        // first boxcar start not yet examined
+    int64_t S_prev;   // S at u - 1 (above threshold)
+    int64_t best_S, best_t;
+};
+constexpr int64_t kTailCap = 1 << 16;
 
 struct SearchArgs {
     const int32_t* D;          // [ndm][pitch]
@@ -131,6 +148,9 @@ struct SearchArgs {
     hp_raw_cand* raw;          // output
     int64_t raw_cap;
     int64_t* raw_count;
+    TailRec* tails;            // scratch [tail_cap]
+    int64_t tail_cap;
+    int64_t* tail_count;
     int* status;
 };
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch);

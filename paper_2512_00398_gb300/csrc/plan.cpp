@@ -29,7 +29,7 @@ struct Layout {
     size_t xt = 0, D = 0, lvl_a = 0, lvl_b = 0, mean = 0, hist = 0, rbucket = 0, rrank = 0,
            mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
            vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
-           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0;
+           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
     size_t total = 0;
     size_t search_begin = 0;   // everything from here on is search/merge scratch
 };
@@ -48,7 +48,7 @@ struct hp_plan {
     int64_t t_gap = 0;
     int w_tol = 0;
     int64_t raw_capacity = (int64_t)1 << 22;
-    int dedisp_cfg = 0;
+    int dedisp_cfg = 3;
     uint64_t timeout_ns = 1000000000ull;
 
     std::vector<int32_t> delays;   // [ndm][nchans]
@@ -65,7 +65,7 @@ struct hp_plan {
     const TileDesc* d_tiles = nullptr;
     const StageDesc* d_stages = nullptr;
     const ChanDesc* d_chans = nullptr;
-    const uint16_t* d_addr = nullptr;
+    const uint32_t* d_addr = nullptr;
     int32_t* d_widths = nullptr;
 
     void* ws_user = nullptr;
@@ -133,7 +133,7 @@ void compute_delays(hp_plan* p) {
 
 // ------------------------------------------------------- dedispersion tiling
 // A DM tile holds up to BD consecutive trials.  For every channel the block
-// stages the input row window [t0 + base, t0 + base + 4*nwords + 4) where
+// stages the input row window [t0 + base, t0 + base + 4*nwords + 16) where
 // base = delay(c, first trial) rounded down to 16 bytes; a trial j of the tile
 // then reads 4-byte words at byte offset rel = delay(c, j) - base, served from
 // one of four byte-shifted copies of the row (rel & 3) so every read is an
@@ -149,15 +149,20 @@ RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT) {
     const int32_t hi = p->delays[(size_t)(d0 + nd - 1) * p->nchans + c];
     g.base = lo & ~15;
     const uint32_t span = (uint32_t)(hi - g.base);
-    g.nwords = (span >> 2) + (uint32_t)(BT / 4);
-    g.bbytes = (uint32_t)align_up(4 * (size_t)g.nwords + 4, 16);
-    g.smem = g.bbytes + (uint32_t)align_up(12 * (size_t)g.nwords, 16);
+    // words per copy, a multiple of 4 so every copy stays 16-byte aligned
+    g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4), 4);
+    g.bbytes = 4 * g.nwords + 16;
+    g.smem = g.bbytes + 12 * g.nwords;
     return g;
+}
+
+uint32_t stage_table_bytes(int nchan, int BD) {
+    return (uint32_t)((size_t)((nchan + 1) / 2) * BD * 2 * sizeof(uint32_t));
 }
 
 uint32_t stage_header(int nchan, int BD) {
     return (uint32_t)(align_up((size_t)nchan * sizeof(ChanDesc), 16) +
-                      align_up((size_t)nchan * BD * sizeof(uint16_t), 16));
+                      align_up(stage_table_bytes(nchan, BD), 16));
 }
 
 int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
@@ -205,32 +210,45 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             sd.chan_begin = (uint32_t)T->chans.size();
             sd.nchan = (uint32_t)n;
             sd.addr_off = (uint32_t)align_up((size_t)n * sizeof(ChanDesc), 16);
+            sd.addr_begin = (uint32_t)T->addr.size();
+            sd.addr_bytes = stage_table_bytes(n, BD);
             uint32_t off = stage_header(n, BD);
-            uint32_t tx = (uint32_t)(n * sizeof(ChanDesc) + n * BD * sizeof(uint16_t));
+            uint32_t tx = (uint32_t)(n * sizeof(ChanDesc)) + sd.addr_bytes;
+            std::vector<uint32_t> word0(n);   // per channel: byte offset of row copy 0
+            std::vector<RowGeom> geo(n);
             for (int i = 0; i < n; ++i) {
                 const int cc = c + i;
                 const RowGeom g = row_geom(p, d0, nd, cc, BT);
+                geo[i] = g;
+                word0[i] = off;
                 ChanDesc cd;
                 cd.c = (uint32_t)cc;
                 cd.goff = g.base;
                 cd.offB = off;
                 cd.nwords = g.nwords;
                 T->chans.push_back(cd);
-                const uint32_t offV = off + g.bbytes;
-                for (int j = 0; j < BD; ++j) {
-                    const int jj = j < nd ? j : 0;
-                    const int32_t rel =
-                        p->delays[(size_t)(d0 + jj) * nch + cc] - g.base;
-                    const uint32_t r = (uint32_t)rel & 3u;
-                    const uint32_t vb = r == 0 ? off : offV + (r - 1) * 4 * g.nwords;
-                    const uint32_t byte_addr = vb + 4 * ((uint32_t)rel >> 2);
-                    T->addr.push_back((uint16_t)(byte_addr >> 2));
-                }
                 tx += g.bbytes;
                 off += g.smem;
                 T->max_reach = std::max<int64_t>(T->max_reach, (int64_t)g.base + g.bbytes);
             }
-            if (off > budget || (off >> 2) > 0xFFFF) return HP_ERR_INVALID_ARG;
+            // table [pair][BD][2]: the byte offset of the word trial j reads first
+            // in each channel of the pair (copy rel & 3, word rel >> 2)
+            for (int pr = 0; pr < (n + 1) / 2; ++pr) {
+                for (int j = 0; j < BD; ++j) {
+                    for (int e = 0; e < 2; ++e) {
+                        const int i = 2 * pr + e < n ? 2 * pr + e : 2 * pr;
+                        const int cc = c + i;
+                        const int jj = j < nd ? j : 0;
+                        const RowGeom& g = geo[i];
+                        const int32_t rel = p->delays[(size_t)(d0 + jj) * nch + cc] - g.base;
+                        const uint32_t r = (uint32_t)rel & 3u;
+                        const uint32_t offV = word0[i] + g.bbytes;
+                        const uint32_t vb = r == 0 ? word0[i] : offV + (r - 1) * 4 * g.nwords;
+                        T->addr.push_back(vb + 4 * ((uint32_t)rel >> 2));
+                    }
+                }
+            }
+            if (off > budget) return HP_ERR_INVALID_ARG;
             sd.tx_bytes = tx;
             T->stages.push_back(sd);
             td.nstages++;
@@ -303,6 +321,8 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
     L.mad = take((size_t)ndm * 8);
     L.sigma = take((size_t)ndm * 8);
     L.tint = take((size_t)ndm * p->nw() * 8);
+    L.tails = take((size_t)kTailCap * sizeof(TailRec));
+    L.tcount = take(8);
     const size_t cap = (size_t)p->raw_capacity;
     // the sort works on whole chunks: key/value scratch is padded to a chunk multiple
     const size_t cap_pad = align_up(cap, (size_t)kSortChunk);
@@ -346,7 +366,7 @@ int ensure_device_tables(hp_plan* p) {
     const size_t o_tiles = take(T.tiles.size() * sizeof(TileDesc));
     const size_t o_stages = take(T.stages.size() * sizeof(StageDesc));
     const size_t o_chans = take(T.chans.size() * sizeof(ChanDesc));
-    const size_t o_addr = take(T.addr.size() * sizeof(uint16_t));
+    const size_t o_addr = take(T.addr.size() * sizeof(uint32_t));
     const size_t o_widths = take(p->widths.size() * sizeof(int32_t));
     const size_t total = off;
     int prev_status = 0;
@@ -364,7 +384,7 @@ int ensure_device_tables(hp_plan* p) {
     std::memcpy(host.data() + o_tiles, T.tiles.data(), T.tiles.size() * sizeof(TileDesc));
     std::memcpy(host.data() + o_stages, T.stages.data(), T.stages.size() * sizeof(StageDesc));
     std::memcpy(host.data() + o_chans, T.chans.data(), T.chans.size() * sizeof(ChanDesc));
-    std::memcpy(host.data() + o_addr, T.addr.data(), T.addr.size() * sizeof(uint16_t));
+    std::memcpy(host.data() + o_addr, T.addr.data(), T.addr.size() * sizeof(uint32_t));
     std::memcpy(host.data() + o_widths, p->widths.data(), p->widths.size() * sizeof(int32_t));
     rc = check_cuda(cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice));
     if (rc) {
@@ -380,7 +400,7 @@ int ensure_device_tables(hp_plan* p) {
     p->d_tiles = (const TileDesc*)(b + o_tiles);
     p->d_stages = (const StageDesc*)(b + o_stages);
     p->d_chans = (const ChanDesc*)(b + o_chans);
-    p->d_addr = (const uint16_t*)(b + o_addr);
+    p->d_addr = (const uint32_t*)(b + o_addr);
     p->d_widths = (int32_t*)(b + o_widths);
     return HP_OK;
 }
@@ -481,6 +501,9 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.raw = raw;
     a.raw_cap = raw_cap;
     a.raw_count = raw_count;
+    a.tails = (TailRec*)(ws + L.tails);
+    a.tail_cap = kTailCap;
+    a.tail_count = (int64_t*)(ws + L.tcount);
     a.status = p->status;
     return a;
 }

@@ -152,23 +152,22 @@ struct BaselineCtx {
     int64_t pre_pitch, H;
 };
 
-struct Walker {
-    int mode;
-    MedianWalker med;
-    MeanWalker mean;
-    __device__ void setup(const BaselineCtx& c, const int32_t* Drow, int64_t n, int trial) {
-        mode = c.mode;
-        if (mode == 0) {
-            med.m = c.knots + (int64_t)trial * c.knot_pitch;
-            med.M = c.M; med.P = c.P; med.half = c.half;
-        } else {
-            mean.D = Drow; mean.pre = c.pre + (int64_t)trial * c.pre_pitch;
-            mean.n = n; mean.H = c.H;
-        }
+// Walker<0>: running-median baseline; Walker<1>: moving-mean baseline.  The
+// mode is uniform per launch, so the kernels are instantiated per mode.
+template <int MODE> struct Walker;
+
+template <> struct Walker<0> : MedianWalker {
+    __device__ void setup(const BaselineCtx& c, const int32_t*, int64_t, int trial) {
+        m = c.knots + (int64_t)trial * c.knot_pitch;
+        M = c.M; P = c.P; half = c.half;
     }
-    __device__ void init(int64_t t) { if (mode == 0) med.init(t); else mean.init(t); }
-    __device__ __forceinline__ int64_t value() const { return mode == 0 ? med.value() : mean.value(); }
-    __device__ __forceinline__ void step() { if (mode == 0) med.step(); else mean.step(); }
+};
+
+template <> struct Walker<1> : MeanWalker {
+    __device__ void setup(const BaselineCtx& c, const int32_t* Drow, int64_t n_, int trial) {
+        D = Drow; pre = c.pre + (int64_t)trial * c.pre_pitch;
+        n = n_; H = c.H;
+    }
 };
 
 // ------------------------------------------------------ mean-mode prefix
@@ -230,9 +229,27 @@ __device__ __forceinline__ int hist_bin(int64_t v) {
     return v < kHistFine ? (int)v : kHistFine + (int)min(v >> 12, (int64_t)(kHistFine - 1));
 }
 
+// The 32 samples of one thread's chunk, with 16-byte loads when the row is
+// 16-byte aligned (pitch a multiple of 4 and an aligned base).
+__device__ __forceinline__ void load_chunk32(const int32_t* __restrict__ row, int64_t t_begin,
+                                             int64_t t_end, bool vec, int32_t (&v)[32]) {
+    if (vec && t_end - t_begin == 32) {
+        const int4* p = reinterpret_cast<const int4*>(row + t_begin);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int4 x = __ldg(p + q);
+            v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = t_begin + q < t_end ? row[t_begin + q] : 0;
+    }
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(256) mad_hist_kernel(const int32_t* __restrict__ D,
                                                        int64_t pitch, int64_t n, BaselineCtx bc,
-                                                       uint32_t* __restrict__ hist) {
+                                                       int vec, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kHistBins];
     const int trial = blockIdx.y;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) h[i] = 0;
@@ -241,14 +258,19 @@ __global__ void __launch_bounds__(256) mad_hist_kernel(const int32_t* __restrict
     const int64_t t_begin = (int64_t)blockIdx.x * kHistChunk + threadIdx.x * 32;
     const int64_t t_end = min(n, t_begin + 32);
     if (t_begin < t_end) {
-        Walker w;
+        int32_t v[32];
+        load_chunk32(row, t_begin, t_end, vec != 0, v);
+        Walker<MODE> w;
         w.setup(bc, row, n, trial);
         w.init(t_begin);
-        for (int64_t t = t_begin; t < t_end; ++t) {
-            int64_t y = (int64_t)row[t] - w.value();
-            if (y < 0) y = -y;
-            atomicAdd(&h[hist_bin(y)], 1u);
-            w.step();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (t_begin + q < t_end) {
+                int64_t y = (int64_t)v[q] - w.value();
+                if (y < 0) y = -y;
+                atomicAdd(&h[hist_bin(y)], 1u);
+                w.step();
+            }
         }
     }
     __syncthreads();
@@ -315,9 +337,10 @@ __global__ void __launch_bounds__(1024) mad_select_kernel(uint32_t* __restrict__
         for (int i = threadIdx.x; i < kHistFine; i += blockDim.x) hrow[i] = 0;
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(256) mad_refine_hist_kernel(const int32_t* __restrict__ D,
                                                               int64_t pitch, int64_t n,
-                                                              BaselineCtx bc,
+                                                              BaselineCtx bc, int vec,
                                                               const int32_t* __restrict__ bucket,
                                                               uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kHistFine];
@@ -330,14 +353,19 @@ __global__ void __launch_bounds__(256) mad_refine_hist_kernel(const int32_t* __r
     const int64_t t_begin = (int64_t)blockIdx.x * kHistChunk + threadIdx.x * 32;
     const int64_t t_end = min(n, t_begin + 32);
     if (t_begin < t_end) {
-        Walker w;
+        int32_t v[32];
+        load_chunk32(row, t_begin, t_end, vec != 0, v);
+        Walker<MODE> w;
         w.setup(bc, row, n, trial);
         w.init(t_begin);
-        for (int64_t t = t_begin; t < t_end; ++t) {
-            int64_t y = (int64_t)row[t] - w.value();
-            if (y < 0) y = -y;
-            if ((y >> 12) == B) atomicAdd(&h[y & 4095], 1u);
-            w.step();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (t_begin + q < t_end) {
+                int64_t y = (int64_t)v[q] - w.value();
+                if (y < 0) y = -y;
+                if ((y >> 12) == B) atomicAdd(&h[y & 4095], 1u);
+                w.step();
+            }
         }
     }
     __syncthreads();
@@ -377,7 +405,7 @@ __global__ void sigma_kernel(const int64_t* __restrict__ mad, int ndm,
 }
 
 // ------------------------------------------------------------ detection
-constexpr int kDetectThreads = 512;
+constexpr int kDetectThreads = 256;
 constexpr int kDetectPer = kDetectTile / kDetectThreads;   // starts per thread
 
 __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* warp_tot) {
@@ -415,24 +443,73 @@ __device__ __forceinline__ void emit(const SearchArgs& a, int trial, int k, int6
     }
 }
 
+// Follow the run of above-threshold starts that begins at ts with the whole
+// warp (32 starts per step).  Returns false with the run's largest S and first
+// position, or true when the run continues past the tile halo: then *tail_u is
+// the first start not yet examined (the run goes on at least to tail_u - 1).
+template <typename BoxcarFn>
+__device__ __forceinline__ bool follow_run(int64_t ts, int64_t last, int64_t base, int64_t len,
+                                           int64_t W, int64_t thr, BoxcarFn boxcar, int lane,
+                                           int64_t* best_S_out, int64_t* best_t_out,
+                                           int64_t* tail_u) {
+    int64_t best_S = LLONG_MIN, best_t = ts;
+    bool tail = false;
+    for (int64_t u0 = ts;; u0 += 32) {
+        const int64_t u = u0 + lane;
+        const bool inr = u <= last && u - base + W <= len;
+        int64_t Su = 0;
+        bool ab = false;
+        if (inr) {
+            Su = boxcar(u);
+            ab = Su >= thr;
+        }
+        const unsigned stop = __ballot_sync(0xffffffffu, !ab);
+        const int first = stop ? __ffs(stop) - 1 : 32;
+        int64_t cs = (lane < first) ? Su : LLONG_MIN;
+        int64_t ct = u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t os = __shfl_down_sync(0xffffffffu, cs, o);
+            const int64_t ot = __shfl_down_sync(0xffffffffu, ct, o);
+            if (os > cs || (os == cs && ot < ct)) { cs = os; ct = ot; }
+        }
+        cs = __shfl_sync(0xffffffffu, cs, 0);
+        ct = __shfl_sync(0xffffffffu, ct, 0);
+        if (cs > best_S) { best_S = cs; best_t = ct; }
+        if (!stop) continue;
+        const int64_t ue = u0 + first;                 // first start not seen above
+        tail = ue <= last && ue - base + W > len;
+        *tail_u = ue;
+        break;
+    }
+    *best_S_out = best_S;
+    *best_t_out = best_t;
+    return tail;
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_constant__ SearchArgs a,
                                                                 BaselineCtx bc) {
     extern __shared__ int64_t P[];   // P[i] = sum of y over samples [base, base + i)
     __shared__ int64_t warp_tot[32];
+    __shared__ int64_t warp_max[32];
+    __shared__ unsigned run_starts[kDetectThreads / 32][kDetectPer];
     const int trial = blockIdx.y;
     const int64_t n = a.nout;
     const int64_t t0 = (int64_t)blockIdx.x * kDetectTile;
     const int64_t base = t0 - 1;
     const int64_t len = min((int64_t)kDetectTile + a.wmax, n - base);
     const int32_t* row = a.D + (int64_t)trial * a.pitch;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // y over [base, base + len) -> P[1 .. len], then a block-wide prefix sum
-    const int64_t per = (len + kDetectThreads - 1) / kDetectThreads;
+    // y over [base, base + len), one contiguous chunk per thread (the exact
+    // baseline walker steps sample by sample; an odd chunk length keeps the
+    // 16 threads of a half-warp on distinct banks), then a block prefix sum
+    const int64_t per = ((len + kDetectThreads - 1) / kDetectThreads) | 1;
     const int64_t i0 = min(len, tid * per), i1 = min(len, i0 + per);
-    int64_t local = 0;
+    int64_t local = 0, ymax = 0;
     if (i0 < i1) {
-        Walker w;
+        Walker<MODE> w;
         w.setup(bc, row, n, trial);
         int64_t s = base + i0;
         if (s < 0) {                       // the slot before sample 0 holds y = 0
@@ -444,10 +521,14 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
             const int64_t y = (int64_t)row[s] - w.value();
             P[s - base + 1] = y;
             local += y;
+            ymax = max(ymax, y < 0 ? -y : y);
             w.step();
         }
     }
-    const int64_t off = block_exclusive_scan(local, warp_tot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ymax = max(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    if (lane == 0) warp_max[warp] = ymax;
+    const int64_t off = block_exclusive_scan(local, warp_tot);   // (synchronises)
     int64_t run = off;
     for (int64_t i = i0; i < i1; ++i) {
         run += P[i + 1];
@@ -455,55 +536,181 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
     }
     if (tid == 0) P[0] = 0;
     __syncthreads();
+    int64_t tile_max = 0;
+    for (int w = 0; w < kDetectThreads / 32; ++w) tile_max = max(tile_max, warp_max[w]);
+    // every boxcar sum of this tile fits int32, so wrapped 32-bit prefix
+    // differences are exact
+    const bool narrow = tile_max * (int64_t)a.wmax < (int64_t)INT32_MAX;
+    const uint32_t* P32 = reinterpret_cast<const uint32_t*>(P);   // low word of P[i]: P32[2 i]
+
+    // starts handled by this thread: t = t0 + j * kDetectThreads + tid
+    const int i_first = tid + 1;                                  // t - base for j = 0
+    uint32_t pr[kDetectPer];
+#pragma unroll
+    for (int j = 0; j < kDetectPer; ++j) {
+        const int i = i_first + j * kDetectThreads;
+        pr[j] = (narrow && i <= len) ? P32[2 * i] : 0u;
+    }
 
     for (int k = 0; k < a.nw; ++k) {
         const int64_t thr_k = a.tint[(int64_t)trial * a.nw + k];
         if (thr_k == kNever) continue;
         const int64_t W = a.widths[k];
+        const int Wi = (int)W;
         const int64_t last = n - W;                     // last valid boxcar start
-        const int64_t ta = t0 + (int64_t)tid * kDetectPer;
-        const int64_t tb = min(ta + kDetectPer, min(t0 + kDetectTile, last + 1));
-        if (ta >= tb) continue;
-        bool prev = false;
-        if (ta > 0) prev = (P[ta - 1 - base + W] - P[ta - 1 - base]) >= thr_k;
-        for (int64_t t = ta; t < tb; ++t) {
-            const int64_t S = P[t - base + W] - P[t - base];
-            const bool above = S >= thr_k;
-            if (above && !prev) {
-                // this thread owns the run that starts at t: follow it to its end
-                int64_t best_t = t, best_S = S, Sp = S;
-                int64_t u = t + 1;
-                bool slow = false;
-                Walker wa, wb;                          // y(u-1) leaving, y(u+W-1) entering
-                for (; u <= last; ++u) {
-                    int64_t Su;
-                    if (!slow && u - base + W <= len) {
-                        Su = P[u - base + W] - P[u - base];
-                    } else {
-                        if (!slow) {
-                            slow = true;
-                            wa.setup(bc, row, n, trial);
-                            wb.setup(bc, row, n, trial);
-                            wa.init(u - 1);
-                            wb.init(u - 1 + W);
-                        }
-                        Su = Sp - ((int64_t)row[u - 1] - wa.value()) +
-                             ((int64_t)row[u - 1 + W] - wb.value());
-                        wa.step();
-                        wb.step();
-                    }
-                    if (Su < thr_k) break;
-                    if (Su > best_S) { best_S = Su; best_t = u; }
-                    Sp = Su;
-                }
-                emit(a, trial, k, best_t, best_S);
+        const int64_t tend = min(t0 + kDetectTile, last + 1);
+        if (t0 >= tend) continue;
+        const int32_t thr32 = (int32_t)min(thr_k, (int64_t)INT32_MAX);
+        auto box64 = [&](int64_t u) { return P[u - base + W] - P[u - base]; };
+        auto box32 = [&](int64_t u) {
+            const int i = (int)(u - base);
+            return (int64_t)(int32_t)(P32[2 * (i + Wi)] - P32[2 * i]);
+        };
+        unsigned any = 0;
+        if (narrow) {
+#pragma unroll
+            for (int j = 0; j < kDetectPer; ++j) {
+                // warp-consecutive starts; a start opens a run if its left
+                // neighbour (the previous lane, or for lane 0 computed here) is below
+                const int i = i_first + j * kDetectThreads;
+                const bool valid = t0 + (int64_t)(i - 1) < tend;
+                const bool above = valid && (int32_t)(P32[2 * (i + Wi)] - pr[j]) >= thr32;
+                bool prev = false;
+                if (lane == 0 && valid && t0 + (int64_t)(i - 1) > 0)
+                    prev = (int32_t)(P32[2 * (i - 1 + Wi)] - P32[2 * (i - 1)]) >= thr32;
+                const unsigned bits = __ballot_sync(0xffffffffu, above);
+                if (lane > 0) prev = (bits >> (lane - 1)) & 1u;
+                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev);
+                if (lane == 0) run_starts[warp][j] = starts;
+                any |= starts;
             }
-            prev = above;
+        } else {
+#pragma unroll 1
+            for (int j = 0; j < kDetectPer; ++j) {
+                const int64_t t = t0 + (int64_t)j * kDetectThreads + tid;
+                const bool valid = t < tend;
+                const bool above = valid && box64(t) >= thr_k;
+                bool prev = false;
+                if (lane == 0 && valid && t > 0) prev = box64(t - 1) >= thr_k;
+                const unsigned bits = __ballot_sync(0xffffffffu, above);
+                if (lane > 0) prev = (bits >> (lane - 1)) & 1u;
+                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev);
+                if (lane == 0) run_starts[warp][j] = starts;
+                any |= starts;
+            }
         }
+        if (!any) continue;
+        __syncwarp();
+        // runs are rare: follow each with the whole warp outside the unrolled loop
+#pragma unroll 1
+        for (int j = 0; j < kDetectPer; ++j) {
+            unsigned starts = run_starts[warp][j];
+            const int64_t tg = t0 + (int64_t)j * kDetectThreads + warp * 32;   // group base
+            while (starts) {
+                const int L = __ffs(starts) - 1;
+                starts &= starts - 1;
+                int64_t bS, bt, tu = 0;
+                const bool tail =
+                    narrow ? follow_run(tg + L, last, base, len, W, thr_k, box32, lane, &bS, &bt, &tu)
+                           : follow_run(tg + L, last, base, len, W, thr_k, box64, lane, &bS, &bt, &tu);
+                if (lane == 0) {
+                    if (!tail) {
+                        emit(a, trial, k, bt, bS);
+                    } else {
+                        // rare: the run leaves the tile halo; tail_kernel finishes it
+                        const unsigned long long q = atomicAdd(
+                            reinterpret_cast<unsigned long long*>(a.tail_count), 1ull);
+                        if ((int64_t)q < a.tail_cap) {
+                            TailRec r;
+                            r.trial = trial;
+                            r.k = k;
+                            r.u = tu;
+                            r.S_prev = box64(tu - 1);
+                            r.best_S = bS;
+                            r.best_t = bt;
+                            a.tails[q] = r;
+                        } else {
+                            latch_status(a.status, HP_ERR_CAND_OVERFLOW);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Runs that leave the detect tile's halo: continue each one sample at a time
+// from the dedispersed row with exact baseline walkers, then emit it.
+template <int MODE>
+__global__ void tail_kernel(const __grid_constant__ SearchArgs a, BaselineCtx bc) {
+    const int64_t cnt = min(*a.tail_count, a.tail_cap);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const TailRec r = a.tails[q];
+        const int64_t n = a.nout;
+        const int32_t* row = a.D + (int64_t)r.trial * a.pitch;
+        const int64_t W = a.widths[r.k];
+        const int64_t last = n - W;
+        const int64_t thr = a.tint[(int64_t)r.trial * a.nw + r.k];
+        int64_t best_S = r.best_S, best_t = r.best_t, Sp = r.S_prev;
+        Walker<MODE> wa, wb;                         // y(v-1) leaving, y(v+W-1) entering
+        wa.setup(bc, row, n, r.trial);
+        wb.setup(bc, row, n, r.trial);
+        wa.init(r.u - 1);
+        wb.init(r.u - 1 + W);
+        for (int64_t v = r.u; v <= last; ++v) {
+            const int64_t Sv = Sp - ((int64_t)row[v - 1] - wa.value()) +
+                               ((int64_t)row[v - 1 + W] - wb.value());
+            wa.step();
+            wb.step();
+            if (Sv < thr) break;
+            if (Sv > best_S) { best_S = Sv; best_t = v; }
+            Sp = Sv;
+        }
+        emit(a, r.trial, r.k, best_t, best_S);
     }
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <int MODE>
+cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStream_t s,
+                           int64_t* nlaunch) {
+    cudaError_t e;
+    const int64_t n = a.nout;
+    const int ndm = a.ndm;
+    const dim3 hgrid((unsigned)ceil_div(n, kHistChunk), ndm);
+    const int vec = ((a.pitch & 3) == 0) && (((uintptr_t)a.D & 15u) == 0);
+    ++*nlaunch;
+    mad_hist_kernel<MODE><<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, vec, a.hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nlaunch;
+    mad_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, n, a.refine_bucket, a.refine_rank, a.mad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nlaunch;
+    mad_refine_hist_kernel<MODE><<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, vec, a.refine_bucket,
+                                                       a.hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nlaunch;
+    mad_refine_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, a.refine_bucket, a.refine_rank, a.mad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nlaunch;
+    sigma_kernel<<<(unsigned)ceil_div(ndm, 128), 128, 0, s>>>(a.mad, ndm, a.widths, a.nw, a.thr,
+                                                              a.sigma, a.tint);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
+    if ((e = cudaFuncSetAttribute(detect_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const dim3 dgrid((unsigned)ceil_div(n, kDetectTile), ndm);
+    ++*nlaunch;
+    detect_kernel<MODE><<<dgrid, kDetectThreads, smem, s>>>(a, bc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nlaunch;
+    tail_kernel<MODE><<<64, 128, 0, s>>>(a, bc);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -513,6 +720,7 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
     const int ndm = a.ndm;
     if (ndm <= 0 || n <= 0) return cudaSuccess;
     if ((e = cudaMemsetAsync(a.raw_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.tail_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.hist, 0, (size_t)ndm * kHistBins * 4, s)) != cudaSuccess) return e;
 
     BaselineCtx bc{};
@@ -569,32 +777,8 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
 
-    const dim3 hgrid((unsigned)ceil_div(n, kHistChunk), ndm);
-    ++*nlaunch;
-    mad_hist_kernel<<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, a.hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nlaunch;
-    mad_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, n, a.refine_bucket, a.refine_rank, a.mad);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nlaunch;
-    mad_refine_hist_kernel<<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, a.refine_bucket, a.hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nlaunch;
-    mad_refine_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, a.refine_bucket, a.refine_rank, a.mad);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nlaunch;
-    sigma_kernel<<<(unsigned)ceil_div(ndm, 128), 128, 0, s>>>(a.mad, ndm, a.widths, a.nw, a.thr,
-                                                              a.sigma, a.tint);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-
-    const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
-    if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    const dim3 dgrid((unsigned)ceil_div(n, kDetectTile), ndm);
-    ++*nlaunch;
-    detect_kernel<<<dgrid, kDetectThreads, smem, s>>>(a, bc);
-    return cudaGetLastError();
+    return a.baseline_mode == 0 ? launch_walkers<0>(a, bc, s, nlaunch)
+                                : launch_walkers<1>(a, bc, s, nlaunch);
 }
 
 }  // namespace hp

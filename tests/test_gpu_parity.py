@@ -246,3 +246,31 @@ def test_fast_full_size_recovery(hp, torch, fast_full):
     bright = [pl for pl in s.pulses if pl.snr >= 10.0]
     missed = [pl for pl in bright if not recovered(pl, got, w, snr_min=w.threshold)]
     assert not missed, missed
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_long_runs_and_tile_edges(hp, torch, mode):
+    """Runs far longer than a detect tile plus its halo (finished by the tail
+    kernel), runs straddling tile boundaries, and a run reaching the last
+    start, compared exactly with the oracle in both baseline modes."""
+    rng = np.random.default_rng(31)
+    nch, nsamps, ts = 64, 60000, 1e-3
+    dms = np.linspace(0, 30, 9).astype(np.float32)
+    widths = np.array([1, 2, 8, 32, 256], np.int32)
+    x = rng.normal(100, 10, size=(nsamps, nch))
+    x[10000:22000] += 12          # a 12 000-sample plateau: runs of ~12 000 starts
+    for edge in (4096 * 5 - 3, 4096 * 8 - 1, 4096 * 9 + 2):
+        x[edge:edge + 6] += 60    # short pulses across tile boundaries
+    x[-400:] += 25                # a run that ends at the series end
+    x = np.clip(np.rint(x), 0, 255).astype(np.uint8)
+    want = oracle.search(x, 1500.0, -4.0, ts, dms, widths, 4.0, baseline_mode=mode,
+                         baseline_s=30.0)
+    p = hp.Plan(nch, 1500.0, -4.0, ts, dms, widths, 4.0, baseline_mode=mode, baseline_s=30.0)
+    fb = torch.from_numpy(x).cuda()
+    D = hp.hp_dedisperse(p, fb)
+    raw_g, sig_g, mad_g = hp.detect(p, D, p.nout(nsamps))
+    assert np.array_equal(sig_g, want.sigma)
+    assert _key(raw_g) == _key(want.raw)
+    assert max(int(r["sample"]) for r in want.raw) > 0
+    got = hp.search(p, fb)
+    _compare_clusters(got, want.clusters, 4.0)
