@@ -28,18 +28,23 @@ constexpr int kKeySampleShift = 5;
 constexpr int64_t kMaxSamples = (int64_t)1 << 38;
 
 // ------------------------------------------------------ dedispersion tiles
-// Thread tile: RD trials x NW words (4 samples each) per thread; WD warps
-// along the trial axis, WT along time.  BD = WD*RD trials, BT = WT*NW*128
-// samples per block, 32*WD*WT threads.
+// Thread tile: RD trials x NW words per thread; WD warps along the trial axis,
+// WT along time; 32*WD*WT threads.  Layout 0 keeps bytes in shared memory
+// (a word = 4 samples, split into 16-bit lanes when summed); layout 1 keeps
+// 16-bit samples (a word = 2 samples, summed as they are).
 constexpr int kDedispStages = 3;         // shared-memory ring of channel stages
 struct DedispConfig {
     int RD, NW, WD, WT;
     int stage_bytes;   // shared memory per stage buffer (kDedispStages per block)
+    int producers;     // 0: every warp stages and computes; > 0: producer warps
+    int layout;        // 0: byte rows + 3 byte-shifted copies; 1: 16-bit even/odd copies;
+                       // 2: byte rows only, aligned in registers (deep copy ring)
+    int stages;        // stage buffers (layout 2; the others use kDedispStages)
     int BD() const { return WD * RD; }
-    int BT() const { return WT * NW * 128; }
+    int BT() const { return WT * NW * (layout == 1 ? 64 : 128); }
     int threads() const { return 32 * WD * WT; }
 };
-constexpr int kNumDedispConfigs = 4;
+constexpr int kNumDedispConfigs = 14;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
 
 // One staged channel row of a DM tile (16 bytes, copied into shared memory).
@@ -47,7 +52,7 @@ struct ChanDesc {
     uint32_t c;        // channel index
     int32_t goff;      // first input sample of the row relative to the time tile
     uint32_t offB;     // byte offset of the row copy in the stage buffer
-    uint32_t nwords;   // 4-byte words per shifted variant
+    uint32_t nwords;   // 32-bit words per shifted / widened copy
 };
 static_assert(sizeof(ChanDesc) == 16, "ChanDesc layout");
 

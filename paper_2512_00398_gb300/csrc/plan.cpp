@@ -48,7 +48,7 @@ struct hp_plan {
     int64_t t_gap = 0;
     int w_tol = 0;
     int64_t raw_capacity = (int64_t)1 << 22;
-    int dedisp_cfg = 3;
+    int dedisp_cfg = 10;
     uint64_t timeout_ns = 1000000000ull;
 
     std::vector<int32_t> delays;   // [ndm][nchans]
@@ -143,16 +143,30 @@ struct RowGeom {
     uint32_t nwords, bbytes, smem;
 };
 
-RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT) {
+RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT, int layout) {
     RowGeom g;
     const int32_t lo = p->delays[(size_t)d0 * p->nchans + c];
     const int32_t hi = p->delays[(size_t)(d0 + nd - 1) * p->nchans + c];
     g.base = lo & ~15;
     const uint32_t span = (uint32_t)(hi - g.base);
-    // words per copy, a multiple of 4 so every copy stays 16-byte aligned
-    g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4), 4);
-    g.bbytes = 4 * g.nwords + 16;
-    g.smem = g.bbytes + 12 * g.nwords;
+    if (layout == 0) {
+        // words of 4 samples per copy, a multiple of 4 so copies stay 16-byte aligned
+        g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4), 4);
+        g.bbytes = 4 * g.nwords + 16;
+        g.smem = g.bbytes + 12 * g.nwords;
+    } else if (layout == 1) {
+        // words of 2 samples per 16-bit copy (even- and odd-aligned), a multiple
+        // of 8; the byte row holds samples 0 .. 2 nwords
+        g.nwords = (uint32_t)align_up((span >> 1) + (uint32_t)(BT / 2), 8);
+        g.bbytes = 2 * g.nwords + 16;
+        g.smem = g.bbytes + 8 * g.nwords;
+    } else {
+        // the byte row alone: a trial reads words (rel >> 2) .. (rel >> 2) + BT/4
+        // and aligns them in registers
+        g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4) + 1, 4);
+        g.bbytes = 4 * g.nwords;
+        g.smem = g.bbytes;
+    }
     return g;
 }
 
@@ -185,12 +199,13 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
         while (nd < BD && d0 + nd < ndm) {
             bool ok = true;
             for (int c = nch - 1; c >= 0 && ok; --c)
-                ok = row_geom(p, d0, nd + 1, c, BT).smem + stage_header(1, BD) <= budget;
+                ok = row_geom(p, d0, nd + 1, c, BT, C.layout).smem + stage_header(1, BD) <= budget;
             if (!ok) break;
             ++nd;
         }
         for (int c = 0; c < nch; ++c)
-            if (row_geom(p, d0, nd, c, BT).smem + stage_header(1, BD) > budget) return HP_ERR_INVALID_ARG;
+            if (row_geom(p, d0, nd, c, BT, C.layout).smem + stage_header(1, BD) > budget)
+                return HP_ERR_INVALID_ARG;
         TileDesc td;
         td.d0 = d0;
         td.nd = nd;
@@ -201,7 +216,7 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             int n = 0;
             uint32_t rows = 0;
             while (c + n < nch && n < kStageMaxChans) {
-                const RowGeom g = row_geom(p, d0, nd, c + n, BT);
+                const RowGeom g = row_geom(p, d0, nd, c + n, BT, C.layout);
                 if (stage_header(n + 1, BD) + rows + g.smem > budget) break;
                 rows += g.smem;
                 ++n;
@@ -218,7 +233,7 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             std::vector<RowGeom> geo(n);
             for (int i = 0; i < n; ++i) {
                 const int cc = c + i;
-                const RowGeom g = row_geom(p, d0, nd, cc, BT);
+                const RowGeom g = row_geom(p, d0, nd, cc, BT, C.layout);
                 geo[i] = g;
                 word0[i] = off;
                 ChanDesc cd;
@@ -241,10 +256,21 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                         const int jj = j < nd ? j : 0;
                         const RowGeom& g = geo[i];
                         const int32_t rel = p->delays[(size_t)(d0 + jj) * nch + cc] - g.base;
-                        const uint32_t r = (uint32_t)rel & 3u;
                         const uint32_t offV = word0[i] + g.bbytes;
-                        const uint32_t vb = r == 0 ? word0[i] : offV + (r - 1) * 4 * g.nwords;
-                        T->addr.push_back(vb + 4 * ((uint32_t)rel >> 2));
+                        if (C.layout == 2) {
+                            // the row's word rel >> 2, alignment rel & 3 in the low bits
+                            T->addr.push_back((word0[i] + 4 * ((uint32_t)rel >> 2)) |
+                                              ((uint32_t)rel & 3u));
+                        } else if (C.layout == 0) {
+                            // byte copy rel & 3 (copy 0 is the row itself), word rel >> 2
+                            const uint32_t r = (uint32_t)rel & 3u;
+                            const uint32_t vb = r == 0 ? word0[i] : offV + (r - 1) * 4 * g.nwords;
+                            T->addr.push_back(vb + 4 * ((uint32_t)rel >> 2));
+                        } else {
+                            // 16-bit copy rel & 1 (even, odd), word rel >> 1
+                            const uint32_t vb = offV + ((uint32_t)rel & 1u) * 4 * g.nwords;
+                            T->addr.push_back(vb + 4 * ((uint32_t)rel >> 1));
+                        }
                     }
                 }
             }
