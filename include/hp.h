@@ -125,7 +125,7 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
 
-#define HP_NUM_DEDISP_CONFIGS 14
+#define HP_NUM_DEDISP_CONFIGS 17
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);

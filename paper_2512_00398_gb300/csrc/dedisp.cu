@@ -35,6 +35,9 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
     {2, 5, 16, 1, 36 * 1024, 1, 2, 6}, // byte rows: 16+1 warps, BD 32, BT 640, 6 buffers
     {2, 3, 8, 2, 36 * 1024, 1, 2, 6},  // byte rows: 16+1 warps, BD 16, BT 768, 6 buffers
     {4, 3, 8, 2, 36 * 1024, 1, 2, 6},  // byte rows: 16+1 warps, BD 32, BT 768, 6 buffers
+    {2, 7, 12, 1, 36 * 1024, 1, 2, 6}, // byte rows: 12+1 warps, BD 24, BT 896, 6 buffers
+    {2, 7, 6, 2, 36 * 1024, 1, 2, 6},  // byte rows: 12+1 warps, BD 12, BT 1792, 6 buffers
+    {2, 5, 12, 1, 36 * 1024, 1, 2, 6}, // byte rows: 12+1 warps, BD 24, BT 640, 6 buffers
 };
 
 namespace {
@@ -893,16 +896,17 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
             return;
         const uint32_t B = sbase + (uint32_t)(b * stage_bytes);
         const StageDesc S = J.stages[T.stage_begin + s];
-        const uint32_t tab = B + S.addr_off + (uint32_t)(wd * RD * 8);
+        const uint32_t tab = B + S.addr_off + (uint32_t)(wd * RD * 16);
+        const uint32_t tb = B + lane_off;
         const uint32_t nchan = S.nchan;
         for (uint32_t c = 0; c < nchan; c += 2) {
             const bool two = c + 1 < nchan;
 #pragma unroll
             for (int r = 0; r < RD; ++r) {
-                const uint2 e = lds64(tab + (c >> 1) * (BD * 8) + r * 8);
-                const uint32_t a0 = B + (e.x & ~3u) + lane_off, a1 = B + (e.y & ~3u) + lane_off;
-                const uint32_t s0 = 0x3210u + 0x1111u * (e.x & 3u);
-                const uint32_t s1 = 0x3210u + 0x1111u * (e.y & 3u);
+                // {offset ch0, offset ch1, selector ch0, selector ch1}
+                const uint4 e = lds128(tab + (c >> 1) * (BD * 16) + r * 16);
+                const uint32_t a0 = tb + e.x, a1 = tb + e.y;
+                const uint32_t s0 = e.z, s1 = e.w;
                 uint32_t w0[NW + 1], w1[NW + 1];
 #pragma unroll
                 for (int i = 0; i <= NW; ++i) w0[i] = lds32(a0 + 4 * i);
@@ -1022,6 +1026,9 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
         case 11: return run_dedisp_rows<2, 5, 16, 1, 6>(b, sb, status, timeout_ns, s);
         case 12: return run_dedisp_rows<2, 3, 8, 2, 6>(b, sb, status, timeout_ns, s);
         case 13: return run_dedisp_rows<4, 3, 8, 2, 6>(b, sb, status, timeout_ns, s);
+        case 14: return run_dedisp_rows<2, 7, 12, 1, 6>(b, sb, status, timeout_ns, s);
+        case 15: return run_dedisp_rows<2, 7, 6, 2, 6>(b, sb, status, timeout_ns, s);
+        case 16: return run_dedisp_rows<2, 5, 12, 1, 6>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

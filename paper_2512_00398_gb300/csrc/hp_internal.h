@@ -44,7 +44,7 @@ struct DedispConfig {
     int BT() const { return WT * NW * (layout == 1 ? 64 : 128); }
     int threads() const { return 32 * WD * WT; }
 };
-constexpr int kNumDedispConfigs = 14;
+constexpr int kNumDedispConfigs = 17;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
 
 // One staged channel row of a DM tile (16 bytes, copied into shared memory).
@@ -66,7 +66,7 @@ struct StageDesc {
     uint32_t addr_off;    // byte offset of the address table in the buffer
     uint32_t tx_bytes;    // bytes landing in shared memory for this stage
     uint32_t addr_begin;  // index of the stage's table in the address array
-    uint32_t addr_bytes;  // table bytes (pairs * BD * 8)
+    uint32_t addr_bytes;  // table bytes (pairs * BD * 8, layout 2: pairs * BD * 16)
 };
 
 struct TileDesc {

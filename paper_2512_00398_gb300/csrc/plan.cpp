@@ -170,13 +170,16 @@ RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT, int layout) {
     return g;
 }
 
-uint32_t stage_table_bytes(int nchan, int BD) {
-    return (uint32_t)((size_t)((nchan + 1) / 2) * BD * 2 * sizeof(uint32_t));
+// Table entries per channel pair and trial: two 32-bit words (layouts 0, 1:
+// byte offsets) or four (layout 2: byte offsets and PRMT selectors).
+uint32_t stage_table_bytes(int nchan, int BD, int layout) {
+    const size_t per = layout == 2 ? 4 : 2;
+    return (uint32_t)((size_t)((nchan + 1) / 2) * BD * per * sizeof(uint32_t));
 }
 
-uint32_t stage_header(int nchan, int BD) {
+uint32_t stage_header(int nchan, int BD, int layout) {
     return (uint32_t)(align_up((size_t)nchan * sizeof(ChanDesc), 16) +
-                      align_up(stage_table_bytes(nchan, BD), 16));
+                      align_up(stage_table_bytes(nchan, BD, layout), 16));
 }
 
 int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
@@ -199,12 +202,12 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
         while (nd < BD && d0 + nd < ndm) {
             bool ok = true;
             for (int c = nch - 1; c >= 0 && ok; --c)
-                ok = row_geom(p, d0, nd + 1, c, BT, C.layout).smem + stage_header(1, BD) <= budget;
+                ok = row_geom(p, d0, nd + 1, c, BT, C.layout).smem + stage_header(1, BD, C.layout) <= budget;
             if (!ok) break;
             ++nd;
         }
         for (int c = 0; c < nch; ++c)
-            if (row_geom(p, d0, nd, c, BT, C.layout).smem + stage_header(1, BD) > budget)
+            if (row_geom(p, d0, nd, c, BT, C.layout).smem + stage_header(1, BD, C.layout) > budget)
                 return HP_ERR_INVALID_ARG;
         TileDesc td;
         td.d0 = d0;
@@ -217,7 +220,7 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             uint32_t rows = 0;
             while (c + n < nch && n < kStageMaxChans) {
                 const RowGeom g = row_geom(p, d0, nd, c + n, BT, C.layout);
-                if (stage_header(n + 1, BD) + rows + g.smem > budget) break;
+                if (stage_header(n + 1, BD, C.layout) + rows + g.smem > budget) break;
                 rows += g.smem;
                 ++n;
             }
@@ -226,8 +229,8 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             sd.nchan = (uint32_t)n;
             sd.addr_off = (uint32_t)align_up((size_t)n * sizeof(ChanDesc), 16);
             sd.addr_begin = (uint32_t)T->addr.size();
-            sd.addr_bytes = stage_table_bytes(n, BD);
-            uint32_t off = stage_header(n, BD);
+            sd.addr_bytes = stage_table_bytes(n, BD, C.layout);
+            uint32_t off = stage_header(n, BD, C.layout);
             uint32_t tx = (uint32_t)(n * sizeof(ChanDesc)) + sd.addr_bytes;
             std::vector<uint32_t> word0(n);   // per channel: byte offset of row copy 0
             std::vector<RowGeom> geo(n);
@@ -247,9 +250,11 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                 T->max_reach = std::max<int64_t>(T->max_reach, (int64_t)g.base + g.bbytes);
             }
             // table [pair][BD][2]: the byte offset of the word trial j reads first
-            // in each channel of the pair (copy rel & 3, word rel >> 2)
+            // in each channel of the pair (copy rel & 3, word rel >> 2); layout 2
+            // appends the two PRMT selectors that align the row to rel & 3
             for (int pr = 0; pr < (n + 1) / 2; ++pr) {
                 for (int j = 0; j < BD; ++j) {
+                    uint32_t sel[2] = {0, 0};
                     for (int e = 0; e < 2; ++e) {
                         const int i = 2 * pr + e < n ? 2 * pr + e : 2 * pr;
                         const int cc = c + i;
@@ -258,9 +263,10 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                         const int32_t rel = p->delays[(size_t)(d0 + jj) * nch + cc] - g.base;
                         const uint32_t offV = word0[i] + g.bbytes;
                         if (C.layout == 2) {
-                            // the row's word rel >> 2, alignment rel & 3 in the low bits
-                            T->addr.push_back((word0[i] + 4 * ((uint32_t)rel >> 2)) |
-                                              ((uint32_t)rel & 3u));
+                            // the row's word rel >> 2; bytes rel & 3 .. 3 + (rel & 3)
+                            // of each word pair are selected by one PRMT
+                            T->addr.push_back(word0[i] + 4 * ((uint32_t)rel >> 2));
+                            sel[e] = 0x3210u + 0x1111u * ((uint32_t)rel & 3u);
                         } else if (C.layout == 0) {
                             // byte copy rel & 3 (copy 0 is the row itself), word rel >> 2
                             const uint32_t r = (uint32_t)rel & 3u;
@@ -271,6 +277,10 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                             const uint32_t vb = offV + ((uint32_t)rel & 1u) * 4 * g.nwords;
                             T->addr.push_back(vb + 4 * ((uint32_t)rel >> 1));
                         }
+                    }
+                    if (C.layout == 2) {
+                        T->addr.push_back(sel[0]);
+                        T->addr.push_back(sel[1]);
                     }
                 }
             }
