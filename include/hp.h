@@ -189,6 +189,56 @@ int hp_merge(hp_plan* plan, const hp_raw_cand* raw_dev, const int64_t* nraw_dev,
              int64_t raw_capacity, const double* sigma_dev, void* stream,
              hp_cand_buf* cand_out);
 
+/* Try every byte-row dedispersion tile shape (HP_PARAM_DEDISP_CONFIG values
+ * 10..) on this input (transpose + dedispersion, two timed passes each after a
+ * warm-up, events on `stream`, synchronising), keep the fastest in the
+ * plan (HP_PARAM_DEDISP_CONFIG) and report it.  best_config / best_ms are
+ * optional host outputs.  The tile shape is the only thing tuned; results do
+ * not depend on it. */
+int hp_plan_autotune(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps, void* stream,
+                     int* best_config, float* best_ms);
+
+/* ------------------------------------------------------------ batching */
+/* Many filterbanks of uneven length, channel count and sampling time searched
+ * together -- the multi-file workload that the paper (Section IV-C) serves
+ * with a two-stage pipeline of CPU threads and task queues.  Here every file's
+ * dedispersion tiles go into ONE kernel launch, the per-file search and merge
+ * chains run side by side on internal streams, and the whole sequence is
+ * captured once into a CUDA graph and replayed while the inputs, sizes and
+ * outputs stay the same.  Results are identical to hp_search per file.
+ *   plans  host array of nfiles (1..HP_BATCH_MAX_FILES) caller-owned plans, one
+ *          per file; they must outlive the batch, and the batch sets their
+ *          dedispersion tile configuration (all files share one). */
+typedef struct hp_batch hp_batch;
+#define HP_BATCH_MAX_FILES 32
+
+int hp_batch_create(hp_batch** out, hp_plan* const* plans, int nfiles);
+int hp_batch_destroy(hp_batch* batch);
+
+/* Use tile configuration `config` for every file (drops a captured graph). */
+int hp_batch_set_config(hp_batch* batch, int config);
+
+/* Time every byte-row tile shape (the configurations that HP_PARAM_DEDISP_CONFIG
+ * values 10.. select) on these inputs, one timed pass each after one warm-up
+ * pass (synchronising), and keep the fastest for the batch and its plans.
+ * Inputs as for hp_batch_search. */
+int hp_batch_autotune(hp_batch* batch, const uint8_t* const* filterbanks_dev,
+                      const int64_t* nsamps, void* stream, int* best_config, float* best_ms);
+
+/* Search every file: filterbanks_dev / nsamps are host arrays of nfiles device
+ * pointers and lengths; cand_out a host array of nfiles output buffers.  The
+ * first call with a given set of arguments runs directly, the second captures
+ * a CUDA graph, later identical calls replay it.  Asynchronous on `stream`. */
+int hp_batch_search(hp_batch* batch, const uint8_t* const* filterbanks_dev, const int64_t* nsamps,
+                    void* stream, hp_cand_buf* cand_out);
+
+/* Wait for `stream`, then return (and clear) the first device-side status of
+ * any of the batch's plans (see hp_plan_sync_status). */
+int hp_batch_sync_status(hp_batch* batch, void* stream);
+
+/* Kernel launches enqueued per hp_batch_search call (graph nodes when replayed). */
+int hp_batch_kernels_per_call(const hp_batch* batch, int64_t* kernels);
+
 /* Per-stage timing and launch accounting (no counterpart in the paper, whose
  * Fig. 2 reports per-stage times of Heimdall).  With HP_PARAM_STAGE_TIMING = 1
  * every stage launch is bracketed by CUDA events recorded on the launching

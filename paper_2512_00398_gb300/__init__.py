@@ -19,8 +19,8 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_PARAM_DEDISP_CONFIG, HP_PARAM_DM_TOL, HP_PARAM_RAW_CAPACITY,
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
-                   STAGE_NAMES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks, Stats, check, lib,
-                   status_str)
+                   STAGE_NAMES, HP_BATCH_MAX_FILES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks,
+                   Stats, check, lib, status_str)
 
 _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASELINE_S,
            "dm_tol": HP_PARAM_DM_TOL, "t_gap": HP_PARAM_T_GAP, "w_tol": HP_PARAM_W_TOL,
@@ -241,6 +241,94 @@ def hp_merge_static(raw, raw_count, sigma, widths, dm_tol=1, t_gap=0, w_tol=None
                                 int(w.size if w_tol is None else w_tol), _stream_ptr(stream),
                                 C.byref(b)), "hp_merge_static")
     return data, count
+
+
+def hp_plan_autotune(plan: Plan, filterbank, stream=None):
+    """Time every dedispersion tile shape on this input and keep the fastest;
+    returns (config, ms)."""
+    _check_fb(plan, filterbank)
+    cfg, ms = C.c_int(0), C.c_float(0.0)
+    check(lib().hp_plan_autotune(plan.handle, C.c_void_p(filterbank.data_ptr()),
+                                 int(filterbank.shape[0]), _stream_ptr(stream), C.byref(cfg),
+                                 C.byref(ms)), "hp_plan_autotune")
+    return int(cfg.value), float(ms.value)
+
+
+class Batch:
+    """Owning handle of an ``hp_batch``: several files searched as one launch
+    sequence (captured into a CUDA graph after the first call)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = C.c_void_p()
+        check(lib().hp_batch_create(C.byref(h), arr, len(self.plans)), "hp_batch_create")
+        self._h = h
+        self._bufs = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise HPError(HP_ERR_INVALID_ARG, "batch already destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().hp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, config: int):
+        check(lib().hp_batch_set_config(self.handle, int(config)), "hp_batch_set_config")
+
+    @staticmethod
+    def _arrays(filterbanks):
+        fbs = (C.c_void_p * len(filterbanks))(*[fb.data_ptr() for fb in filterbanks])
+        ns = (C.c_int64 * len(filterbanks))(*[int(fb.shape[0]) for fb in filterbanks])
+        return fbs, ns
+
+    def autotune(self, filterbanks, stream=None):
+        fbs, ns = self._arrays(filterbanks)
+        cfg, ms = C.c_int(0), C.c_float(0.0)
+        check(lib().hp_batch_autotune(self.handle, fbs, ns, _stream_ptr(stream), C.byref(cfg),
+                                      C.byref(ms)), "hp_batch_autotune")
+        return int(cfg.value), float(ms.value)
+
+    def search_async(self, filterbanks, stream=None, outs=None, capacity: int = 1 << 16):
+        """Enqueue the batch; returns the list of device (data, count) pairs."""
+        if len(filterbanks) != len(self.plans):
+            raise HPError(HP_ERR_INVALID_ARG, "one filterbank per plan")
+        for p, fb in zip(self.plans, filterbanks):
+            _check_fb(p, fb)
+        if outs is None:
+            outs = [new_cand_buf(capacity, fb.device) for fb in filterbanks]
+        bufs = (CandBuf * len(outs))(*[_buf(d, c, d.numel() // CAND_DTYPE.itemsize)
+                                       for d, c in outs])
+        fbs, ns = self._arrays(filterbanks)
+        check(lib().hp_batch_search(self.handle, fbs, ns, _stream_ptr(stream), bufs),
+              "hp_batch_search")
+        return outs
+
+    def sync_status(self, stream=None) -> int:
+        return int(lib().hp_batch_sync_status(self.handle, _stream_ptr(stream)))
+
+    def kernels_per_call(self) -> int:
+        k = C.c_int64(0)
+        check(lib().hp_batch_kernels_per_call(self.handle, C.byref(k)), "hp_batch_kernels_per_call")
+        return int(k.value)
+
+    def search(self, filterbanks, stream=None, capacity: int = 1 << 16):
+        """Search every file and return one merged-candidate array per file."""
+        outs = self.search_async(filterbanks, stream, capacity=capacity)
+        st = self.sync_status(stream)
+        if st != HP_OK:
+            raise HPError(st, "hp_batch_search (device)")
+        return [cands_to_numpy(d, c) for d, c in outs]
 
 
 def hp_plan_sync_status(plan: Plan, stream=None) -> int:

@@ -49,7 +49,12 @@ assert CAND_DTYPE.itemsize == 48 and RAW_DTYPE.itemsize == 24
 EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_param",
            "hp_plan_get_param", "hp_plan_delays", "hp_plan_max_delay", "hp_plan_workspace_bytes",
            "hp_plan_bind_workspace", "hp_search", "hp_dedisperse", "hp_detect", "hp_merge",
-           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks", "hp_merge_static")
+           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks", "hp_merge_static",
+           "hp_plan_autotune", "hp_batch_create", "hp_batch_destroy", "hp_batch_set_config",
+           "hp_batch_autotune", "hp_batch_search", "hp_batch_sync_status",
+           "hp_batch_kernels_per_call")
+
+HP_BATCH_MAX_FILES = 32
 
 #: raw-candidate limit of hp_merge_static
 HP_MERGE_STATIC_MAX_RAW = 65536
@@ -107,6 +112,14 @@ def lib() -> C.CDLL:
             L.hp_measure_peaks.argtypes = [C.POINTER(Peaks)]
             L.hp_merge_static.argtypes = [vp, vp, i64, vp, vp, i32, i32, i64, i32, vp,
                                           C.POINTER(CandBuf)]
+            L.hp_plan_autotune.argtypes = [vp, vp, i64, vp, C.POINTER(i32), C.POINTER(C.c_float)]
+            L.hp_batch_create.argtypes = [C.POINTER(vp), vp, i32]
+            L.hp_batch_destroy.argtypes = [vp]
+            L.hp_batch_set_config.argtypes = [vp, i32]
+            L.hp_batch_autotune.argtypes = [vp, vp, vp, vp, C.POINTER(i32), C.POINTER(C.c_float)]
+            L.hp_batch_search.argtypes = [vp, vp, vp, vp, vp]
+            L.hp_batch_sync_status.argtypes = [vp, vp]
+            L.hp_batch_kernels_per_call.argtypes = [vp, C.POINTER(i64)]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32

@@ -44,12 +44,12 @@ namespace {
 
 constexpr int kTT = 64;
 
-__global__ void __launch_bounds__(256) transpose_kernel(const uint8_t* __restrict__ x,
-                                                        int64_t nsamps, int nch, int vec,
-                                                        uint8_t* __restrict__ xt, int64_t pitch) {
+// One 64 x 64 byte tile of the transpose: rows t0.., channels c0.. of x
+// [nsamps][nch] -> xt [nch][pitch] (zero beyond nsamps).
+__device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, int64_t nsamps,
+                                               int nch, int vec, uint8_t* __restrict__ xt,
+                                               int64_t pitch, int64_t t0, int c0) {
     __shared__ __align__(16) uint8_t tile[kTT][kTT + 16];
-    const int64_t t0 = (int64_t)blockIdx.x * kTT;
-    const int c0 = blockIdx.y * kTT;
     const int tid = threadIdx.x;
     {
         const int row = tid >> 2, seg = tid & 3;
@@ -84,6 +84,23 @@ __global__ void __launch_bounds__(256) transpose_kernel(const uint8_t* __restric
     }
 }
 
+__global__ void __launch_bounds__(256) transpose_kernel(const uint8_t* __restrict__ x,
+                                                        int64_t nsamps, int nch, int vec,
+                                                        uint8_t* __restrict__ xt, int64_t pitch) {
+    transpose_tile(x, nsamps, nch, vec, xt, pitch, (int64_t)blockIdx.x * kTT, blockIdx.y * kTT);
+}
+
+// Every file of a batch in one launch: block b handles tile b - prefix[j] of file j.
+__global__ void __launch_bounds__(256) transpose_batch_kernel(const __grid_constant__ TransposeBatch tb) {
+    const int64_t blk = blockIdx.x;
+    int j = 0;
+    while (j + 1 < tb.njobs && tb.prefix[j + 1] <= blk) ++j;
+    const TransposeJob& J = tb.jobs[j];
+    const int64_t item = blk - tb.prefix[j];
+    const int64_t tt = item % J.ttiles;
+    const int ct = (int)(item / J.ttiles);
+    transpose_tile(J.x, J.nsamps, J.nch, J.vec, J.xt, J.pitch, tt * kTT, ct * kTT);
+}
 
 // 32-bit shared-memory accesses on shared-window addresses.
 __device__ __forceinline__ uint32_t lds32(uint32_t a) {
@@ -1005,6 +1022,27 @@ cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8
     const int vec = ((nchans & 15) == 0) && (((uintptr_t)x & 15u) == 0);
     dim3 grid((unsigned)((xt_pitch + kTT - 1) / kTT), (unsigned)((nchans + kTT - 1) / kTT));
     transpose_kernel<<<grid, 256, 0, s>>>(x, nsamps, nchans, vec, xt, xt_pitch);
+    return cudaGetLastError();
+}
+
+TransposeJob make_transpose_job(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
+                                int64_t xt_pitch) {
+    TransposeJob J;
+    J.x = x;
+    J.nsamps = nsamps;
+    J.nch = nchans;
+    J.vec = ((nchans & 15) == 0) && (((uintptr_t)x & 15u) == 0);
+    J.xt = xt;
+    J.pitch = xt_pitch;
+    J.ttiles = (xt_pitch + kTT - 1) / kTT;
+    J.ctiles = (nchans + kTT - 1) / kTT;
+    return J;
+}
+
+cudaError_t launch_transpose_batch(const TransposeBatch& tb, cudaStream_t s) {
+    const int64_t total = tb.prefix[tb.njobs];
+    if (total <= 0) return cudaSuccess;
+    transpose_batch_kernel<<<(unsigned)total, 256, 0, s>>>(tb);
     return cudaGetLastError();
 }
 

@@ -111,12 +111,31 @@ struct DedispBatch {
     DedispJob jobs[kMaxJobs];
 };
 
+// One file of a batched transpose.
+struct TransposeJob {
+    const uint8_t* x;
+    int64_t nsamps;
+    int32_t nch, vec;
+    uint8_t* xt;
+    int64_t pitch;
+    int64_t ttiles;            // 64-sample tiles along time (of the padded pitch)
+    int32_t ctiles, pad_;      // 64-channel tiles
+};
+struct TransposeBatch {
+    int32_t njobs, pad_;
+    int64_t prefix[kMaxJobs + 1];   // tiles of files before j (tiles = ttiles * ctiles)
+    TransposeJob jobs[kMaxJobs];
+};
+
 // ------------------------------------------------------------- launchers
 // All return cudaSuccess or the launch error.
 cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
                              int64_t xt_pitch, cudaStream_t s);
 cudaError_t launch_dedisp(int cfg, const DedispBatch& batch, int* status, uint64_t timeout_ns,
                           cudaStream_t s);
+TransposeJob make_transpose_job(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
+                                int64_t xt_pitch);
+cudaError_t launch_transpose_batch(const TransposeBatch& tb, cudaStream_t s);
 
 // A run that left the detect tile's halo, to be finished by tail_kernel.
 struct TailRec {

@@ -274,3 +274,49 @@ def test_long_runs_and_tile_edges(hp, torch, mode):
     assert max(int(r["sample"]) for r in want.raw) > 0
     got = hp.search(p, fb)
     _compare_clusters(got, want.clusters, 4.0)
+
+
+def _small_batch(nfiles=5):
+    from paper_2512_00398_gb300 import workloads
+    return workloads.batch(nfiles=nfiles, len_lo=1 << 16, len_hi=1 << 17, dm_hi=300.0,
+                           trial_density=0.4, wmax=256)
+
+
+def test_batch_matches_per_file_search(hp, torch):
+    """Uneven files (channels, lengths, sampling times) searched as one batch:
+    eager first call, captured graph, replays and after autotuning, each equal
+    to hp_search of that file alone."""
+    files = _small_batch()
+    gens = [w.generate() for w in files]
+    fbs = [torch.from_numpy(g.data).cuda() for g in gens]
+    plans = [_plan(hp, w) for w in files]
+    want = [hp.search(p, fb) for p, fb in zip(plans, fbs)]
+    assert sum(len(x) for x in want) > 0
+    b = hp.Batch(plans)
+    for _ in range(3):
+        got = b.search(fbs)
+        for g, w_ in zip(got, want):
+            assert np.array_equal(g, w_)
+    assert b.kernels_per_call() > 0
+    cfg, ms = b.autotune(fbs)
+    assert 0 <= cfg < hp.HP_NUM_DEDISP_CONFIGS and ms > 0
+    for _ in range(2):
+        got = b.search(fbs)
+        for g, w_ in zip(got, want):
+            assert np.array_equal(g, w_)
+    # a different output set re-captures
+    outs = [hp.new_cand_buf(1 << 12) for _ in fbs]
+    b.search_async(fbs, outs=outs)
+    assert b.sync_status() == hp.HP_OK
+    for (d, c), w_ in zip(outs, want):
+        assert np.array_equal(hp.cands_to_numpy(d, c), w_)
+    b.close()
+
+
+def test_plan_autotune_keeps_results(hp, torch, tiny):
+    w, s, fb = tiny
+    p = _plan(hp, w)
+    before = hp.search(p, fb)
+    cfg, ms = hp.hp_plan_autotune(p, fb)
+    assert p.get_param("dedisp_config") == cfg and ms > 0
+    assert np.array_equal(hp.search(p, fb), before)
