@@ -99,6 +99,11 @@ def lib():
                                             C.c_int64, vp, vp, vp]
             L.hpo_search.argtypes = [vp, C.c_int64, _P(_Params), vp, C.c_int64, vp, vp,
                                      C.c_int64, vp, vp, vp]
+            L.hpo_detect_window.argtypes = [vp, C.c_int64, C.c_int, C.c_double, vp, C.c_int,
+                                            C.c_float, C.c_int64, vp, vp, C.c_int64, vp,
+                                            C.c_int64, vp]
+            L.hpo_search_window.argtypes = [vp, C.c_int64, _P(_Params), C.c_int64, C.c_int64,
+                                            vp, vp, vp, C.c_int64, vp, vp, C.c_int64, vp]
             _lib = L
     return _lib
 
@@ -290,3 +295,80 @@ def search_trials(D: np.ndarray, d_begin: int, tsamp, widths, thr, baseline_mode
     if rc:
         raise ValueError(f"hpo_search_trials rc={rc}")
     return raw[: nr.value].copy(), sig, md
+
+
+# ----------------------------------------------------- c9 streamed search
+def detect_window(y: np.ndarray, d: int, sigma: float, widths, thr: float, nwin: int,
+                  carry_in=None, t_offset: int = 0, cap: int = 1 << 20):
+    """Runs of one series reported by the window rule (Sections III-B, V-C;
+    reading in hp_oracle.c).  Returns (raw candidates, carry_out[nw])."""
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    cin = None if carry_in is None else np.ascontiguousarray(carry_in, dtype=np.uint8)
+    cout = np.zeros(w.size, dtype=np.uint8)
+    out = np.empty(cap, dtype=RAW_DTYPE)
+    n = C.c_int64(0)
+    rc = lib().hpo_detect_window(_ptr(y), int(y.size), int(d), float(sigma), _ptr(w),
+                                 int(w.size), float(thr), int(nwin),
+                                 None if cin is None else _ptr(cin), _ptr(cout), int(t_offset),
+                                 _ptr(out), int(cap), C.byref(n))
+    if rc:
+        raise ValueError(f"hpo_detect_window rc={rc}")
+    return out[: n.value].copy(), cout
+
+
+def search_window(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, nwin: int,
+                  t_offset: int, carry_in=None, baseline_mode=0, baseline_s=2.0, dm_tol=1,
+                  t_gap=0, w_tol=None, cap=1 << 22):
+    """One gulp's buffer searched with the window rule; returns (raw, clusters,
+    carry_out[ndm][nw])."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    nsamps, nch = x.shape
+    p, keep = _params(nch, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode,
+                      baseline_s, dm_tol, t_gap, w_tol)
+    ndm, nw = keep[0].size, keep[1].size
+    cin = None if carry_in is None else np.ascontiguousarray(carry_in, dtype=np.uint8)
+    cout = np.zeros((ndm, nw), dtype=np.uint8)
+    raw = np.empty(cap, dtype=RAW_DTYPE)
+    cl = np.empty(cap, dtype=CLUSTER_DTYPE)
+    nr, nc = C.c_int64(0), C.c_int64(0)
+    rc = lib().hpo_search_window(_ptr(x), int(nsamps), C.byref(p), int(nwin), int(t_offset),
+                                 None if cin is None else _ptr(cin), _ptr(cout), _ptr(raw),
+                                 int(cap), C.byref(nr), _ptr(cl), int(cap), C.byref(nc))
+    if rc:
+        raise ValueError(f"hpo_search_window rc={rc}")
+    return raw[: nr.value].copy(), cl[: nc.value].copy(), cout
+
+
+def gulp_geometry(g: int, gulp: int, maxd: int, wmax: int):
+    """Buffer of gulp g (Sections III-B, V-C; reading in hp_oracle.c):
+    (B0, E, nwin) with input samples [B0, E) searched and boxcar starts
+    [0, nwin) its window; nwin <= 0 means the gulp is not searched."""
+    H = maxd + wmax - 1
+    E = (g + 1) * gulp
+    B0 = max(0, g * gulp - H)
+    return B0, E, E - H - B0
+
+
+def stream_search(x: np.ndarray, gulp: int, f_top, chan_bw, tsamp, dm_list, widths, thr,
+                  baseline_mode=0, baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None):
+    """A beam's whole series x[nsamps][nchans] searched gulp by gulp; the last
+    partial gulp is dropped.  Returns one dict per gulp: g, B0, nwin, raw,
+    clusters (samples in the beam's dedispersed time)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    nch = x.shape[1]
+    tab = delays(nch, f_top, chan_bw, tsamp, dm_list)
+    maxd = int(tab.max())
+    wmax = int(np.max(widths))
+    out, carry = [], None
+    for g in range(x.shape[0] // gulp):
+        B0, E, nwin = gulp_geometry(g, gulp, maxd, wmax)
+        if nwin <= 0:
+            out.append({"g": g, "B0": B0, "nwin": 0, "raw": np.empty(0, RAW_DTYPE),
+                        "clusters": np.empty(0, CLUSTER_DTYPE)})
+            continue
+        raw, cl, carry = search_window(x[B0:E], f_top, chan_bw, tsamp, dm_list, widths, thr,
+                                       nwin, B0, carry, baseline_mode, baseline_s, dm_tol, t_gap,
+                                       w_tol)
+        out.append({"g": g, "B0": B0, "nwin": nwin, "raw": raw, "clusters": cl})
+    return out

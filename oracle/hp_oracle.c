@@ -356,6 +356,82 @@ int hpo_detect_trial(const int64_t* y, int64_t n, int d, double sigma,
 }
 
 /* ------------------------------------------------------------------------
+ * Step c9a: detection inside one gulp's window (streamed search).
+ * Section III-B explains that a long observation is searched chunk by chunk
+ * and that neighbouring chunks must overlap in time to keep a dispersed
+ * signal whole across a chunk boundary; Section V-C searches a long file in
+ * chunks of 256K samples.  The paper gives no rule for the overlap or for
+ * candidates near a boundary.  The reading used here (also in
+ * hpo_search_window below): the searched buffer's boxcar starts [0, nwin)
+ * form this gulp's window; later starts are look-ahead.  The runs of
+ * above-threshold starts are found exactly as in hpo_detect_trial over every
+ * valid start [0, n - W], and a run is reported iff its first start lies in
+ * the window, unless it begins at start 0 while carry_in[k] says that the
+ * previous window ended inside a run (that run was reported by the previous
+ * gulp).  carry_out[k] = 1 iff start nwin - 1 is above threshold.  Reported
+ * samples are shifted by t_offset (the buffer's first dedispersed sample in
+ * the stream).
+ * ---------------------------------------------------------------------- */
+static int detect_window_into(const int64_t* y, int64_t n, int d, double sigma,
+                              const int32_t* widths, int nw, float thr, int64_t nwin,
+                              const uint8_t* carry_in, uint8_t* carry_out, int64_t t_offset,
+                              raw_vec* rv) {
+    for (int k = 0; k < nw; ++k) carry_out[k] = 0;
+    if (!(sigma > 0.0)) return 0;
+    int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!P) return -1;
+    P[0] = 0;
+    for (int64_t i = 0; i < n; ++i) P[i + 1] = P[i] + y[i];
+    for (int k = 0; k < nw; ++k) {
+        int64_t W = widths[k];
+        if (W > n) continue;
+        double lim = (double)thr * sigma * sqrt((double)W);
+        int64_t last = n - W;
+        if (nwin >= 1 && nwin - 1 <= last)
+            carry_out[k] = (double)(P[nwin - 1 + W] - P[nwin - 1]) >= lim;
+        int64_t t = 0;
+        while (t <= last) {
+            int64_t S = P[t + W] - P[t];
+            if (!((double)S >= lim)) { ++t; continue; }
+            int64_t first = t, best_t = t, best_S = S;
+            for (++t; t <= last; ++t) {
+                int64_t S2 = P[t + W] - P[t];
+                if (!((double)S2 >= lim)) break;
+                if (S2 > best_S) { best_S = S2; best_t = t; }
+            }
+            if (first >= nwin) break;                        /* past the window */
+            if (first == 0 && carry_in && carry_in[k]) continue;   /* reported before */
+            hpo_raw r;
+            r.dm_idx = d;
+            r.width_idx = k;
+            r.sample = best_t + t_offset;
+            r.S = best_S;
+            r.snr = (double)best_S / (sigma * sqrt((double)W));
+            if (raw_push(rv, r)) { free(P); return -1; }
+        }
+    }
+    free(P);
+    return 0;
+}
+
+int hpo_detect_window(const int64_t* y, int64_t n, int d, double sigma, const int32_t* widths,
+                      int nw, float thr, int64_t nwin, const uint8_t* carry_in,
+                      uint8_t* carry_out, int64_t t_offset, hpo_raw* out, int64_t cap,
+                      int64_t* nout) {
+    raw_vec rv = {0, 0, 0};
+    if (detect_window_into(y, n, d, sigma, widths, nw, thr, nwin, carry_in, carry_out, t_offset,
+                           &rv)) {
+        free(rv.v);
+        return HPO_ERR_ARG;
+    }
+    *nout = rv.n;
+    int64_t m = rv.n < cap ? rv.n : cap;
+    if (m > 0) memcpy(out, rv.v, sizeof(hpo_raw) * (size_t)m);
+    free(rv.v);
+    return rv.n > cap ? HPO_ERR_OVERFLOW : HPO_OK;
+}
+
+/* ------------------------------------------------------------------------
  * Step c7: candidate merging and clustering (Section II-B, "Candate Merging
  * and Clustering"; Algorithm 1, last stage).  Candidates are ordered by
  * (dm_idx, sample, width_idx).  Two candidates are friends iff
@@ -561,4 +637,66 @@ int hpo_search(const uint8_t* x, int64_t nsamps, const hpo_params* p,
     free(D);
     if (rc) return rc;
     return hpo_merge(raw, *nraw, p->widths, p->dm_tol, p->t_gap, p->w_tol, cl, cl_cap, ncl);
+}
+
+/* ------------------------------------------------------------------------
+ * Step c9b: one gulp of a streamed search (Sections III-B, V-C; reading as
+ * in detect_window_into).  x holds the searched buffer: input samples
+ * [B0, E) of the beam, nsamps = E - B0 = nwin + maxd + Wmax - 1 (or fewer
+ * leading samples for the first gulps, B0 = 0).  The buffer is searched as a
+ * plain series (dedispersion, per-trial baseline, MAD sigma, boxcars), runs
+ * are kept by the window rule, samples are shifted by t_offset = B0, and the
+ * gulp's raw candidates are merged on their own.  carry_in / carry_out are
+ * [ndm][nw] flags (carry_in may be NULL for the first searched gulp).
+ * ---------------------------------------------------------------------- */
+int hpo_search_window(const uint8_t* x, int64_t nsamps, const hpo_params* p, int64_t nwin,
+                      int64_t t_offset, const uint8_t* carry_in, uint8_t* carry_out,
+                      hpo_raw* raw, int64_t raw_cap, int64_t* nraw,
+                      hpo_cluster* cl, int64_t cl_cap, int64_t* ncl) {
+    *nraw = 0;
+    *ncl = 0;
+    int32_t* delays = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->ndm * (size_t)p->nchans);
+    if (!delays) return HPO_ERR_ARG;
+    int rc = hpo_delays(p->nchans, p->f_top, p->chan_bw, p->tsamp, p->dm_list, p->ndm, delays);
+    if (rc) { free(delays); return rc; }
+    int32_t maxd = hpo_max_delay(delays, p->ndm, p->nchans);
+    int wmax = 0;
+    for (int k = 0; k < p->nw; ++k) if (p->widths[k] > wmax) wmax = p->widths[k];
+    int64_t nout = nsamps - maxd;
+    if (nwin < 1 || nout != nwin + wmax - 1) { free(delays); return HPO_ERR_ARG; }
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->ndm * (size_t)nout);
+    if (!D) { free(delays); return HPO_ERR_ARG; }
+    rc = hpo_dedisperse_rows(x, nsamps, p->nchans, delays, 0, p->ndm, nout, D);
+    free(delays);
+    if (rc) { free(D); return rc; }
+    int64_t win = hpo_baseline_window(p->baseline_s, p->tsamp);
+    raw_vec* per = (raw_vec*)calloc((size_t)p->ndm, sizeof(raw_vec));
+    if (!per) { free(D); return HPO_ERR_ARG; }
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+    for (int d = 0; d < p->ndm; ++d) {
+        int64_t* y = (int64_t*)malloc(sizeof(int64_t) * (size_t)nout);
+        if (!y) { bad = 1; continue; }
+        if (hpo_subtract_baseline(D + (int64_t)d * nout, nout, p->baseline_mode, win, y)) bad = 1;
+        double sigma = hpo_sigma_from_mad(hpo_mad(y, nout));
+        if (detect_window_into(y, nout, d, sigma, p->widths, p->nw, p->thr, nwin,
+                               carry_in ? carry_in + (int64_t)d * p->nw : NULL,
+                               carry_out + (int64_t)d * p->nw, t_offset, &per[d]))
+            bad = 1;
+        free(y);
+    }
+    free(D);
+    int64_t tot = 0;
+    for (int d = 0; d < p->ndm; ++d) {
+        for (int64_t i = 0; i < per[d].n; ++i) {
+            if (tot < raw_cap) raw[tot] = per[d].v[i];
+            ++tot;
+        }
+        free(per[d].v);
+    }
+    free(per);
+    *nraw = tot;
+    if (bad) return HPO_ERR_ARG;
+    if (tot > raw_cap) return HPO_ERR_OVERFLOW;
+    return hpo_merge(raw, tot, p->widths, p->dm_tol, p->t_gap, p->w_tol, cl, cl_cap, ncl);
 }

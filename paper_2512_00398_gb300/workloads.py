@@ -121,3 +121,45 @@ def batch(nfiles: int = 16, seed0: int = 100, len_lo: int = 1 << 17, len_hi: int
         pulses = _random_pulses(obs, rng, npul, dm_hi, 0.1e-3, 20e-3, 8.0, 30.0, max(t_hi, 0.1))
         files.append(Workload(f"batch{i}", obs, dms, synth.widths_pow2(wmax), 6.0, s, pulses))
     return files
+
+
+def stream_tiny(nbeams: int = 3, ngulps: int = 8, gulp: int = 4096, seed0: int = 200,
+                npulses: int = 4) -> list:
+    """Beams for the streamed-search tests: the tiny band (128 ch, 64 us),
+    ngulps * gulp samples each (one continuous series per beam), DM 0-400,
+    widths 1..64, pulses of 8-12 sigma per channel at random DM and time."""
+    beams = []
+    for b in range(nbeams):
+        s = seed0 + b
+        obs = synth.Observation(nchans=128, f_top=1500.0, chan_bw=-1.953125, tsamp=64e-6,
+                                nsamps=ngulps * gulp, mean=128.0, sigma=16.0)
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([s, 12])))
+        t_hi = obs.nsamps * obs.tsamp - _max_delay_s(obs, 400.0) - 0.02
+        pulses = []
+        for _ in range(npulses):
+            dm = float(rng.uniform(20.0, 380.0))
+            fwhm = float(math.exp(rng.uniform(math.log(128e-6), math.log(2e-3))))
+            t0 = float(rng.uniform(0.02, max(t_hi, 0.05)))
+            pulses.append(synth.Pulse(dm, t0, fwhm, float(rng.uniform(8.0, 12.0)) * obs.sigma))
+        beams.append(Workload(f"stream{b}", obs, synth.dm_list_uniform(0.0, 400.0, 100),
+                              synth.widths_pow2(64), 6.0, s, pulses))
+    return beams
+
+
+def serve(nbeams: int = 19, gulp: int = 65536, seconds: float = 600.0, seed0: int = 300,
+          ndm_target: int = 1500, dm_hi: float = 2000.0, wmax: int = 4096) -> list:
+    """The 19-beam stream: each beam the FAST band (4096 ch, 49.152 us), DM
+    0-2000 on the smearing grid (~1500 trials), widths 1..4096, whole gulps of
+    `gulp` samples covering `seconds`, about one pulse per beam-minute."""
+    beams = []
+    for b in range(nbeams):
+        s = seed0 + b
+        ng = max(1, int(round(seconds / (gulp * FAST_BAND["tsamp"]))))
+        obs = synth.Observation(nsamps=ng * gulp, mean=128.0, sigma=12.0, **FAST_BAND)
+        dms = synth.dm_list_smearing(obs, 0.0, dm_hi, ndm_target)
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([s, 13])))
+        npul = max(1, int(round(obs.duration / 60.0)))
+        t_hi = obs.duration - 0.05
+        pulses = _random_pulses(obs, rng, npul, dm_hi, 0.1e-3, 20e-3, 8.0, 30.0, t_hi)
+        beams.append(Workload(f"beam{b}", obs, dms, synth.widths_pow2(wmax), 6.0, s, pulses))
+    return beams

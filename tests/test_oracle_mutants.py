@@ -42,6 +42,14 @@ MUTANTS = {
     "merge_dm_tol": ("c[j].dm_idx <= c[i].dm_idx + dm_tol;", "c[j].dm_idx < c[i].dm_idx + dm_tol;"),
     "merge_rep_last_tie": ("if (c[i].snr > o->snr) {", "if (c[i].snr >= o->snr) {"),
     "merge_t_hi": ("if (e > o->t_hi) o->t_hi = e;", "if (c[i].sample > o->t_hi) o->t_hi = c[i].sample;"),
+    # streamed search (window rule, carry, time offset)
+    "stream_window_inclusive": ("if (first >= nwin) break;", "if (first > nwin) break;"),
+    "stream_no_carry": ("if (first == 0 && carry_in && carry_in[k]) continue;",
+                        "if (0 && first == 0 && carry_in && carry_in[k]) continue;"),
+    "stream_carry_at_nwin": ("carry_out[k] = (double)(P[nwin - 1 + W] - P[nwin - 1]) >= lim;",
+                             "carry_out[k] = (double)(P[nwin + W] - P[nwin]) >= lim;"),
+    "stream_no_offset": ("r.sample = best_t + t_offset;", "r.sample = best_t;"),
+    "stream_peak_first_start": ("if (first == 0 && carry_in", "best_t = first;\n            if (first == 0 && carry_in"),
 }
 
 
@@ -54,7 +62,8 @@ def source():
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name, source, tmp_path):
     find, repl = MUTANTS[name]
-    assert source.count(find) == 1, f"mutation site for {name} not unique / missing"
+    # a site shared by the plain and the streamed detection is mutated in both
+    assert source.count(find) >= 1, f"mutation site for {name} missing"
     csrc = tmp_path / "mutant.c"
     csrc.write_text(source.replace(find, repl))
     so = tmp_path / "libmutant.so"
@@ -62,6 +71,7 @@ def test_pins_catch_mutant(name, source, tmp_path):
                     "-ffp-contract=off", str(csrc), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, HPO_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_stream.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
