@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 16-file batched-vs-plain measurement")
     ap.add_argument("--batch-files", type=int, default=16)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the 19-beam streamed (serving) measurement")
+    ap.add_argument("--serve-beams", type=int, default=19)
+    ap.add_argument("--serve-seconds", type=float, default=40.0,
+                    help="seconds of real-time stream per beam")
     return ap.parse_args()
 
 
@@ -317,6 +322,8 @@ def run_ours(args):
         plan.close()
         torch.cuda.empty_cache()
         line["batch"] = run_batch(args, hp, torch, stream)
+    if world == 1 and not args.no_serve:
+        line["serve"] = run_serve(args, hp, torch)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -401,8 +408,105 @@ def run_batch(args, hp, torch, stream):
         "steps": steps,
     }
     del fbs
+    for p in plans:
+        p.close()
     torch.cuda.empty_cache()
     return res
+
+
+# ------------------------------------------------------------- serving
+def run_serve(args, hp, torch):
+    """The 19-beam stream: 4096 ch, 49.152 us, DM 0-2000, gulps of 65 536
+    samples (3.22 s).  Phase 1 pushes every beam's gulps at the real-time rate
+    (one gulp per beam every 3.22 s, each beam's arrival jittered by 0-20 ms)
+    and reports the gulp latency (push -> candidates in host memory).  Phase 2
+    pushes a backlog of gulps at once and reports the sustained throughput.
+    Gulp data cycle through a pool of 8 distinct synthetic gulps in pinned
+    host memory (generating 19 beams x minutes of data would take longer than
+    the measurement)."""
+    import threading
+    from paper_2512_00398_gb300 import workloads
+    G = 65536
+    nb = args.serve_beams
+    beams = workloads.serve(nbeams=nb, gulp=G, seconds=args.serve_seconds)
+    w = beams[0]
+    o = w.obs
+    pool_n = 8
+    poolw = workloads.serve(nbeams=1, gulp=G, seconds=pool_n * G * o.tsamp, seed0=900)[0]
+    pool_np = poolw.generate(threads=min(16, os.cpu_count() or 8)).data
+    pool = torch.from_numpy(pool_np).pin_memory()
+    del pool_np
+    gulps = [pool[i * G:(i + 1) * G] for i in range(pool_n)]
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    tg = G * o.tsamp
+    budget = 120 * (1 << 30)
+    st = hp.Stream(plan, nbeams=nb, gulp=G, hbm_budget=budget, cand_capacity=4096)
+    info0 = st.stats()
+    H = info0["tail_samples"]
+
+    def collect(n, out):
+        while len(out) < n:
+            r = st.poll(timeout_ms=600000)
+            if r is None:
+                raise RuntimeError("stream stalled")
+            if r[0]["status"] != hp.HP_OK:
+                raise hp.HPError(r[0]["status"], "stream gulp")
+            out.append(r[0])
+
+    # phase 1: real time
+    ng = max(1, int(round(args.serve_seconds / tg)))
+    rng = np.random.default_rng(17)
+    jit = rng.uniform(0.0, 0.020, size=(ng, nb))
+    res1 = []
+    t0 = time.perf_counter() + 0.2
+
+    def producer():
+        for g in range(ng):
+            for b in np.argsort(jit[g]):
+                t = t0 + (g + 1) * tg + jit[g, b]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                st.push(int(b), gulps[(int(b) * 3 + g) % pool_n])
+
+    th = threading.Thread(target=producer)
+    th.start()
+    collect(ng * nb, res1)
+    th.join()
+    searched = [r for r in res1 if r["window_len"] > 0]
+    lat = np.array([r["latency_s"] for r in searched])
+    units1 = sum(r["window_len"] for r in searched) * w.ndm
+    # phase 2: a backlog of 6 gulps per beam pushed at once
+    nb2 = 6
+    res2 = []
+    t = time.perf_counter()
+    for g in range(ng, ng + nb2):
+        for b in range(nb):
+            st.push(b, gulps[(b * 3 + g) % pool_n])
+    collect(nb2 * nb, res2)
+    wall2 = time.perf_counter() - t
+    units2 = sum(r["window_len"] for r in res2) * w.ndm
+    stats = st.stats()
+    st.close()
+    plan.close()
+    del pool, gulps
+    return {
+        "workload": f"{nb} beams x {o.nchans} ch, {o.tsamp * 1e6:.3f} us, gulps of {G} samples "
+                    f"({tg:.3f} s), {w.ndm} trials on DM 0-{float(w.dm_list[-1]):.0f}, boxcars "
+                    f"1..{int(w.widths[-1])}, tail {H} samples, budget {budget >> 30} GiB; "
+                    f"data: {pool_n} distinct synthetic gulps in pinned host memory, cycled",
+        "realtime": {"seconds": ng * tg, "gulps": len(res1), "searched": len(searched),
+                     "latency_p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+                     "latency_p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+                     "latency_max_s": float(lat.max()) if lat.size else None,
+                     "gulp_s": tg,
+                     "rtf_p99": float(tg / np.percentile(lat, 99)) if lat.size else None,
+                     "value": units1 / (ng * tg), "unit": METRIC},
+        "saturated": {"gulps": len(res2), "wall_s": wall2, "value": units2 / wall2,
+                      "unit": METRIC, "rtf": len(res2) * tg / wall2},
+        "steps": stats["steps"], "max_batch_seen": stats["max_batch_seen"],
+        "beam_slots": stats["beam_slots"], "device_gib": stats["device_bytes"] / (1 << 30),
+    }
 
 
 # --------------------------------------------------------- reference arm

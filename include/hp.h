@@ -291,6 +291,103 @@ int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_dev, int64_t
  * HP_ERR_CAND_OVERFLOW or HP_ERR_TIMEOUT.  Synchronises the stream. */
 int hp_plan_sync_status(hp_plan* plan, void* stream);
 
+/* ----------------------------------------------------------- streaming */
+/* Many beams searched as their data arrive, gulp by gulp.  Sections III-B and
+ * V-C of the paper search long observations in chunks whose time segments
+ * overlap so that a dispersed pulse stays whole across a chunk boundary, and
+ * overlap transfers with computation by double buffering (Section IV-C); the
+ * paper gives the overlap only in words.  The rule used here, for gulps of G
+ * samples and H = max_delay + widest boxcar - 1:
+ *   - gulp g of a beam (input samples [g G, (g+1) G)) is searched as one
+ *     series over input [B0, E), E = (g+1) G, B0 = max(0, g G - H): the last
+ *     H samples of earlier gulps stay resident on the device (the tail);
+ *     baseline and sigma are those of a plain search of that buffer;
+ *   - its window is dedispersed samples [B0, B0 + nwin), nwin = E - H - B0;
+ *     the Wmax - 1 samples after it are look-ahead.  A gulp with E <= H has
+ *     no window (nwin <= 0) and only fills the tail;
+ *   - a run of above-threshold boxcar starts is reported by the gulp whose
+ *     window holds its first start, its peak taken inside that buffer; a run
+ *     that the previous window ended inside is not reported again;
+ *   - each gulp's raw candidates are merged on their own (as hp_merge), with
+ *     samples in the beam's dedispersed time (window start + offset).
+ * Continuous batching: a native scheduler thread takes the gulps that have
+ * arrived from every admitted beam (at most one per beam) into one step --
+ * one transpose and one dedispersion launch over all of them, then per gulp
+ * the search and merge on side streams and the copy of its candidates to host
+ * memory -- and keeps up to two steps in flight, so gulps that arrive while a
+ * step runs join the next.  Beams are admitted in order of their first push
+ * while the device budget has room for their tails; the others wait until an
+ * admitted beam ends.  A beam's results do not depend on the other beams. */
+typedef struct hp_stream hp_stream;
+#define HP_STREAM_MAX_BEAMS 1024
+#define HP_STREAM_EMPTY 1   /* hp_stream_poll: no result within the timeout */
+
+typedef struct {
+    int32_t nbeams;          /* beam ids 0 .. nbeams-1 (1..HP_STREAM_MAX_BEAMS) */
+    int32_t max_batch;       /* gulps per step, 1..HP_BATCH_MAX_FILES (0: min(nbeams, 32)) */
+    int64_t gulp;            /* samples per gulp, >= 64 and >= H / 62 */
+    int64_t hbm_budget;      /* device bytes the stream may allocate (0: no limit) */
+    int64_t cand_capacity;   /* merged candidates kept per gulp, >= 1 */
+    int64_t raw_capacity;    /* raw candidates per gulp, >= 1024 */
+} hp_stream_config;
+
+typedef struct {
+    int32_t beam;
+    int32_t status;          /* HP_OK or the device-side status of the gulp's step */
+    int64_t gulp_index;      /* 0, 1, ... in push order of the beam */
+    int64_t window_start;    /* B0: first dedispersed sample of the window */
+    int64_t window_len;      /* nwin, 0 when the gulp had no window */
+    int64_t ncand;           /* merged candidates of the gulp (may exceed what is kept) */
+    double latency_s;        /* hp_stream_push -> candidates in host memory */
+    int32_t batch_size;      /* gulps in the step that searched it */
+    int32_t pad_;
+} hp_gulp_result;
+
+typedef struct {
+    int64_t steps;           /* batched steps completed */
+    int64_t gulps;           /* gulps completed */
+    int32_t beam_slots;      /* beams the budget holds at once */
+    int32_t max_batch;
+    int32_t admitted;        /* beams holding a slot now */
+    int32_t waiting;         /* beams waiting for a slot */
+    int64_t device_bytes;    /* bytes allocated by the stream */
+    int64_t tail_samples;    /* H */
+    int64_t max_batch_seen;
+} hp_stream_stats;
+
+/* Open a stream.  The plan (caller-owned, not used by the stream afterwards)
+ * supplies the band, trials, widths, threshold and parameters; the stream
+ * keeps its own copy.  Allocates everything it will use: per step slot a
+ * search workspace for G + H samples and a candidate buffer, per beam slot a
+ * ring of ceil(H/G) + 2 gulps and two [ndm][nw] carry arrays.  HP_ERR_OOM when
+ * the budget does not hold one beam slot and one step slot. */
+int hp_stream_open(hp_stream** out, const hp_plan* plan, const hp_stream_config* config);
+
+/* Queue the next gulp of `beam`: nsamps == gulp samples of nchans bytes each
+ * ([nsamps][nchans], host memory, pinned for asynchronous copies).  The
+ * memory must stay valid and unchanged until hp_stream_poll has returned
+ * this gulp's result.  Returns at once (HP_ERR_INVALID_ARG for an ended beam
+ * or a wrong size; the stream's first CUDA error once one occurred). */
+int hp_stream_push(hp_stream* s, int beam, const uint8_t* gulp_host, int64_t nsamps);
+
+/* No more gulps for `beam`: its slot is released once its queued gulps are
+ * done, and the longest-waiting beam takes it. */
+int hp_stream_end_beam(hp_stream* s, int beam);
+
+/* Wait up to timeout_ms (< 0: forever) for the next finished gulp, in order
+ * of completion: fills *result and copies min(ncand, cand_cap, cand_capacity)
+ * candidates to host memory `cands`.  HP_STREAM_EMPTY when none finished. */
+int hp_stream_poll(hp_stream* s, hp_gulp_result* result, hp_cand* cands, int64_t cand_cap,
+                   int timeout_ms);
+
+int hp_stream_get_stats(hp_stream* s, hp_stream_stats* out);
+
+/* Stop the stream: queued gulps that no step has taken are dropped, the steps
+ * in flight are waited for, unread results are discarded and everything the
+ * stream allocated is freed.  (To finish a stream, poll until every pushed
+ * gulp's result has arrived, then close.) */
+int hp_stream_close(hp_stream* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
                    STAGE_NAMES, HP_BATCH_MAX_FILES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks,
-                   Stats, check, lib, status_str)
+                   Stats, HP_STREAM_EMPTY, HP_STREAM_MAX_BEAMS, check, lib, status_str)
+from . import _lib as _lib_mod
 
 _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASELINE_S,
            "dm_tol": HP_PARAM_DM_TOL, "t_gap": HP_PARAM_T_GAP, "w_tol": HP_PARAM_W_TOL,
@@ -329,6 +330,89 @@ class Batch:
         if st != HP_OK:
             raise HPError(st, "hp_batch_search (device)")
         return [cands_to_numpy(d, c) for d, c in outs]
+
+
+class Stream:
+    """Owning handle of an ``hp_stream``: beams pushed gulp by gulp, searched in
+    batched steps by the library's scheduler thread, results polled back.
+
+    A pushed gulp's host array is kept referenced here until its result has
+    been polled (the library copies from it asynchronously)."""
+
+    def __init__(self, plan: Plan, nbeams: int, gulp: int, hbm_budget: int = 0,
+                 max_batch: int = 0, cand_capacity: int = 4096, raw_capacity: int = 1 << 18):
+        cfg = _lib_mod.StreamConfig(int(nbeams), int(max_batch), int(gulp), int(hbm_budget),
+                                    int(cand_capacity), int(raw_capacity))
+        h = C.c_void_p()
+        check(lib().hp_stream_open(C.byref(h), plan.handle, C.byref(cfg)), "hp_stream_open")
+        self._h = h
+        self.nchans = plan.nchans
+        self.gulp = int(gulp)
+        self.cand_capacity = int(cand_capacity)
+        self._held = {}
+        self._next = [0] * int(nbeams)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise HPError(HP_ERR_INVALID_ARG, "stream already closed")
+        return self._h
+
+    def push(self, beam: int, gulp):
+        """gulp: uint8 [gulp][nchans], a numpy array or a (pinned) CPU tensor."""
+        if hasattr(gulp, "data_ptr"):
+            ptr, n = gulp.data_ptr(), gulp.shape[0]
+            ok = gulp.is_contiguous() and gulp.numel() == self.gulp * self.nchans
+        else:
+            gulp = np.ascontiguousarray(gulp, dtype=np.uint8)
+            ptr, n = gulp.ctypes.data, gulp.shape[0]
+            ok = gulp.size == self.gulp * self.nchans
+        if not ok:
+            raise HPError(HP_ERR_INVALID_ARG, "gulp must be [gulp][nchans] contiguous uint8")
+        check(lib().hp_stream_push(self.handle, int(beam), C.c_void_p(ptr), int(n)),
+              "hp_stream_push")
+        self._held[(int(beam), self._next[beam])] = gulp
+        self._next[beam] += 1
+
+    def end_beam(self, beam: int):
+        check(lib().hp_stream_end_beam(self.handle, int(beam)), "hp_stream_end_beam")
+
+    def poll(self, timeout_ms: int = -1):
+        """Next finished gulp as (info dict, candidates), or None on timeout."""
+        r = _lib_mod.GulpResult()
+        out = np.empty(self.cand_capacity, dtype=CAND_DTYPE)
+        rc = lib().hp_stream_poll(self.handle, C.byref(r), out.ctypes.data_as(C.c_void_p),
+                                  self.cand_capacity, int(timeout_ms))
+        if rc == HP_STREAM_EMPTY:
+            return None
+        check(rc, "hp_stream_poll")
+        self._held.pop((int(r.beam), int(r.gulp_index)), None)
+        info = {f: getattr(r, f) for f, _ in _lib_mod.GulpResult._fields_ if f != "pad_"}
+        n = min(int(r.ncand), self.cand_capacity)
+        return info, out[:n].copy()
+
+    def stats(self) -> dict:
+        st = _lib_mod.StreamStats()
+        check(lib().hp_stream_get_stats(self.handle, C.byref(st)), "hp_stream_get_stats")
+        return {f: getattr(st, f) for f, _ in _lib_mod.StreamStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().hp_stream_close(self._h)
+            self._h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def hp_plan_sync_status(plan: Plan, stream=None) -> int:

@@ -52,7 +52,11 @@ EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_pa
            "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks", "hp_merge_static",
            "hp_plan_autotune", "hp_batch_create", "hp_batch_destroy", "hp_batch_set_config",
            "hp_batch_autotune", "hp_batch_search", "hp_batch_sync_status",
-           "hp_batch_kernels_per_call")
+           "hp_batch_kernels_per_call", "hp_stream_open", "hp_stream_push", "hp_stream_end_beam",
+           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close")
+
+HP_STREAM_MAX_BEAMS = 1024
+HP_STREAM_EMPTY = 1
 
 HP_BATCH_MAX_FILES = 32
 
@@ -78,6 +82,25 @@ class Peaks(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("stage_ms", C.c_double * HP_NUM_STAGES), ("stage_calls", C.c_int64 * HP_NUM_STAGES),
                 ("kernel_launches", C.c_int64)]
+
+
+class StreamConfig(C.Structure):
+    _fields_ = [("nbeams", C.c_int32), ("max_batch", C.c_int32), ("gulp", C.c_int64),
+                ("hbm_budget", C.c_int64), ("cand_capacity", C.c_int64),
+                ("raw_capacity", C.c_int64)]
+
+
+class GulpResult(C.Structure):
+    _fields_ = [("beam", C.c_int32), ("status", C.c_int32), ("gulp_index", C.c_int64),
+                ("window_start", C.c_int64), ("window_len", C.c_int64), ("ncand", C.c_int64),
+                ("latency_s", C.c_double), ("batch_size", C.c_int32), ("pad_", C.c_int32)]
+
+
+class StreamStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("gulps", C.c_int64), ("beam_slots", C.c_int32),
+                ("max_batch", C.c_int32), ("admitted", C.c_int32), ("waiting", C.c_int32),
+                ("device_bytes", C.c_int64), ("tail_samples", C.c_int64),
+                ("max_batch_seen", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -120,6 +143,12 @@ def lib() -> C.CDLL:
             L.hp_batch_search.argtypes = [vp, vp, vp, vp, vp]
             L.hp_batch_sync_status.argtypes = [vp, vp]
             L.hp_batch_kernels_per_call.argtypes = [vp, C.POINTER(i64)]
+            L.hp_stream_open.argtypes = [C.POINTER(vp), vp, C.POINTER(StreamConfig)]
+            L.hp_stream_push.argtypes = [vp, i32, vp, i64]
+            L.hp_stream_end_beam.argtypes = [vp, i32]
+            L.hp_stream_poll.argtypes = [vp, C.POINTER(GulpResult), vp, i64, i32]
+            L.hp_stream_get_stats.argtypes = [vp, C.POINTER(StreamStats)]
+            L.hp_stream_close.argtypes = [vp]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32

@@ -45,10 +45,14 @@ namespace {
 constexpr int kTT = 64;
 
 // One 64 x 64 byte tile of the transpose: rows t0.., channels c0.. of x
-// [nsamps][nch] -> xt [nch][pitch] (zero beyond nsamps).
+// [nsamps][nch] -> xt [nch][pitch] (zero beyond nsamps).  With ring_len > 0
+// row t is absolute sample a0 + t of a ring of ring_slots slots of ring_len
+// rows (a streamed beam's recent gulps).
 __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, int64_t nsamps,
                                                int nch, int vec, uint8_t* __restrict__ xt,
-                                               int64_t pitch, int64_t t0, int c0) {
+                                               int64_t pitch, int64_t t0, int c0,
+                                               int64_t ring_len = 0, int64_t a0 = 0,
+                                               int ring_slots = 1) {
     __shared__ __align__(16) uint8_t tile[kTT][kTT + 16];
     const int tid = threadIdx.x;
     {
@@ -57,12 +61,18 @@ __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, in
         const int c = c0 + seg * 16;
         uint4 q = make_uint4(0, 0, 0, 0);
         if (t < nsamps) {
+            int64_t r = t;
+            if (ring_len > 0) {
+                const int64_t a = a0 + t;
+                r = (a / ring_len) % ring_slots * ring_len + a % ring_len;
+            }
+            const uint8_t* xr = x + r * nch;
             if (vec && c + 16 <= nch) {
-                q = __ldg(reinterpret_cast<const uint4*>(x + t * nch + c));
+                q = __ldg(reinterpret_cast<const uint4*>(xr + c));
             } else {
                 uint8_t v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = (c + i < nch) ? x[t * nch + c + i] : 0;
+                for (int i = 0; i < 16; ++i) v[i] = (c + i < nch) ? xr[c + i] : 0;
                 memcpy(&q, v, 16);
             }
         }
@@ -99,7 +109,8 @@ __global__ void __launch_bounds__(256) transpose_batch_kernel(const __grid_const
     const int64_t item = blk - tb.prefix[j];
     const int64_t tt = item % J.ttiles;
     const int ct = (int)(item / J.ttiles);
-    transpose_tile(J.x, J.nsamps, J.nch, J.vec, J.xt, J.pitch, tt * kTT, ct * kTT);
+    transpose_tile(J.x, J.nsamps, J.nch, J.vec, J.xt, J.pitch, tt * kTT, ct * kTT, J.ring_len,
+                   J.a0, J.ring_slots);
 }
 
 // 32-bit shared-memory accesses on shared-window addresses.
@@ -1028,6 +1039,10 @@ cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8
 TransposeJob make_transpose_job(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
                                 int64_t xt_pitch) {
     TransposeJob J;
+    J.ring_len = 0;
+    J.a0 = 0;
+    J.ring_slots = 1;
+    J.pad2_ = 0;
     J.x = x;
     J.nsamps = nsamps;
     J.nch = nchans;

@@ -113,6 +113,11 @@ struct DedispBatch {
 
 // One file of a batched transpose.
 struct TransposeJob {
+    // row t of the input is x + t * nch, or with ring_len > 0 the row of
+    // absolute sample a = a0 + t in a ring of ring_slots slots of ring_len rows:
+    // x + ((a / ring_len) % ring_slots * ring_len + a % ring_len) * nch
+    int64_t ring_len, a0;
+    int32_t ring_slots, pad2_;
     const uint8_t* x;
     int64_t nsamps;
     int32_t nch, vec;
@@ -176,6 +181,15 @@ struct SearchArgs {
     int64_t tail_cap;
     int64_t* tail_count;
     int* status;
+    // streamed search (one gulp's buffer): runs are reported only when their
+    // first start t < nwin, and not when t == 0 while carry_in[trial][k] is
+    // set; carry_out[trial][k] = start nwin - 1 above threshold (carry_in and
+    // carry_out are distinct [ndm][nw] arrays, or null).  Reported samples are
+    // t + t_offset.  A plain search has nwin = nout, no carries, offset 0.
+    int64_t nwin;
+    const uint8_t* carry_in;
+    uint8_t* carry_out;
+    int64_t t_offset;
 };
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch);
 

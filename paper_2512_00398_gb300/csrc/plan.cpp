@@ -11,7 +11,7 @@
 #include <new>
 #include <vector>
 
-#include "hp_internal.h"
+#include "plan_internal.h"
 
 using namespace hp;
 
@@ -22,68 +22,9 @@ constexpr double kKDM = 4148.808;   // s MHz^2 pc^-1 cm^3
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int64_t round_up64(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-    int64_t nsamps = 0, nout = 0;
-    int64_t xt_pitch = 0, dpitch = 0;
-    int64_t lvl_pitch_a = 0, lvl_pitch_b = 0, mean_pitch = 0;
-    size_t xt = 0, D = 0, lvl_a = 0, lvl_b = 0, mean = 0, hist = 0, rbucket = 0, rrank = 0,
-           mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
-           vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
-           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
-    size_t total = 0;
-    size_t search_begin = 0;   // everything from here on is search/merge scratch
-};
-
 }  // namespace
 
-struct hp_plan {
-    int nchans = 0;
-    double f_top = 0, chan_bw = 0, tsamp = 0;
-    std::vector<float> dm_list;
-    std::vector<int32_t> widths;
-    float thr = 0;
-    int baseline_mode = 0;
-    double baseline_s = 2.0;
-    int dm_tol = 1;
-    int64_t t_gap = 0;
-    int w_tol = 0;
-    int64_t raw_capacity = (int64_t)1 << 22;
-    int dedisp_cfg = 10;
-    uint64_t timeout_ns = 1000000000ull;
-
-    std::vector<int32_t> delays;   // [ndm][nchans]
-    int32_t maxd = 0, wmax = 0;
-
-    DedispTiling tiling;           // for dedisp_cfg
-
-    // device state
-    int device = -1;
-    void* tables = nullptr;        // plan-owned constant tables + status word
-    size_t tables_bytes = 0;
-    int tables_cfg = -1;
-    int* status = nullptr;
-    const TileDesc* d_tiles = nullptr;
-    const StageDesc* d_stages = nullptr;
-    const ChanDesc* d_chans = nullptr;
-    const uint32_t* d_addr = nullptr;
-    int32_t* d_widths = nullptr;
-
-    void* ws_user = nullptr;
-    size_t ws_user_bytes = 0;
-    void* ws_own = nullptr;
-    size_t ws_own_bytes = 0;
-
-    // stage timing (events on the launching stream) and launch accounting
-    bool timing = false;
-    std::vector<cudaEvent_t> ev[HP_NUM_STAGES];   // pairs (begin, end)
-    int ev_used[HP_NUM_STAGES] = {0, 0, 0, 0};
-    int64_t launches = 0;
-
-    int ndm() const { return (int)dm_list.size(); }
-    int nw() const { return (int)widths.size(); }
-};
-
-namespace {
+namespace hp {
 
 int check_cuda(cudaError_t e) {
     if (e == cudaSuccess) return HP_OK;
@@ -541,6 +482,10 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.tail_cap = kTailCap;
     a.tail_count = (int64_t*)(ws + L.tcount);
     a.status = p->status;
+    a.nwin = nout;
+    a.carry_in = nullptr;
+    a.carry_out = nullptr;
+    a.t_offset = 0;
     return a;
 }
 

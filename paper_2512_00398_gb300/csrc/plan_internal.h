@@ -1,0 +1,95 @@
+// plan_internal.h -- the plan object and the host helpers that the plan,
+// batch and stream runtimes share (plan.cpp, stream.cpp).  Not part of the
+// public C ABI (include/hp.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+// Byte offsets of every array of a search workspace for one input length.
+struct Layout {
+    int64_t nsamps = 0, nout = 0;
+    int64_t xt_pitch = 0, dpitch = 0;
+    int64_t lvl_pitch_a = 0, lvl_pitch_b = 0, mean_pitch = 0;
+    size_t xt = 0, D = 0, lvl_a = 0, lvl_b = 0, mean = 0, hist = 0, rbucket = 0, rrank = 0,
+           mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
+           vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
+           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
+    size_t total = 0;
+    size_t search_begin = 0;   // everything from here on is search/merge scratch
+};
+
+}  // namespace hp
+
+struct hp_plan {
+    int nchans = 0;
+    double f_top = 0, chan_bw = 0, tsamp = 0;
+    std::vector<float> dm_list;
+    std::vector<int32_t> widths;
+    float thr = 0;
+    int baseline_mode = 0;
+    double baseline_s = 2.0;
+    int dm_tol = 1;
+    int64_t t_gap = 0;
+    int w_tol = 0;
+    int64_t raw_capacity = (int64_t)1 << 22;
+    int dedisp_cfg = 10;
+    uint64_t timeout_ns = 1000000000ull;
+
+    std::vector<int32_t> delays;   // [ndm][nchans]
+    int32_t maxd = 0, wmax = 0;
+
+    hp::DedispTiling tiling;           // for dedisp_cfg
+
+    // device state
+    int device = -1;
+    void* tables = nullptr;        // plan-owned constant tables + status word
+    size_t tables_bytes = 0;
+    int tables_cfg = -1;
+    int* status = nullptr;
+    const hp::TileDesc* d_tiles = nullptr;
+    const hp::StageDesc* d_stages = nullptr;
+    const hp::ChanDesc* d_chans = nullptr;
+    const uint32_t* d_addr = nullptr;
+    int32_t* d_widths = nullptr;
+
+    void* ws_user = nullptr;
+    size_t ws_user_bytes = 0;
+    void* ws_own = nullptr;
+    size_t ws_own_bytes = 0;
+
+    // stage timing (events on the launching stream) and launch accounting
+    bool timing = false;
+    std::vector<cudaEvent_t> ev[HP_NUM_STAGES];   // pairs (begin, end)
+    int ev_used[HP_NUM_STAGES] = {0, 0, 0, 0};
+    int64_t launches = 0;
+
+    int ndm() const { return (int)dm_list.size(); }
+    int nw() const { return (int)widths.size(); }
+};
+
+namespace hp {
+
+int check_cuda(cudaError_t e);
+int ensure_device_tables(hp_plan* p);
+int ensure_workspace(hp_plan* p, size_t need, uint8_t** base);
+Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp);
+int64_t xt_pitch_for(int64_t nsamps);
+int validate_search_input(const hp_plan* p, const void* ptr, int64_t nsamps);
+DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_t* out,
+                   int64_t out_pitch, int64_t nout);
+SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int32_t* D,
+                            int64_t pitch, int64_t nout, hp_raw_cand* raw, int64_t raw_cap,
+                            int64_t* raw_count);
+MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw_cand* raw,
+                          const int64_t* nraw, int64_t raw_cap, const double* sigma,
+                          hp_cand_buf* out);
+
+}  // namespace hp

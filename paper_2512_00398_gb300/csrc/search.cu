@@ -437,7 +437,7 @@ __device__ __forceinline__ void emit(const SearchArgs& a, int trial, int k, int6
         hp_raw_cand c;
         c.dm_idx = trial;
         c.width_idx = k;
-        c.sample = t;
+        c.sample = t + a.t_offset;
         c.S = S;
         a.raw[idx] = c;
     }
@@ -552,13 +552,22 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
         pr[j] = (narrow && i <= len) ? P32[2 * i] : 0u;
     }
 
+    // the block that holds start nwin - 1 reports the carry flags
+    const bool carry_here = a.carry_out && a.nwin - 1 >= t0 && a.nwin - 1 < t0 + kDetectTile;
     for (int k = 0; k < a.nw; ++k) {
         const int64_t thr_k = a.tint[(int64_t)trial * a.nw + k];
-        if (thr_k == kNever) continue;
+        if (thr_k == kNever) {
+            if (carry_here && tid == 0) a.carry_out[(int64_t)trial * a.nw + k] = 0;
+            continue;
+        }
+        // a run at start 0 continues one the previous gulp already reported
+        const bool cin = a.carry_in && t0 == 0 && a.carry_in[(int64_t)trial * a.nw + k];
         const int64_t W = a.widths[k];
         const int Wi = (int)W;
         const int64_t last = n - W;                     // last valid boxcar start
         const int64_t tend = min(t0 + kDetectTile, last + 1);
+        if (carry_here && tid == 0 && a.nwin - 1 >= tend)   // start nwin - 1 not valid
+            a.carry_out[(int64_t)trial * a.nw + k] = 0;
         if (t0 >= tend) continue;
         const int32_t thr32 = (int32_t)min(thr_k, (int64_t)INT32_MAX);
         auto box64 = [&](int64_t u) { return P[u - base + W] - P[u - base]; };
@@ -580,7 +589,10 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
                     prev = (int32_t)(P32[2 * (i - 1 + Wi)] - P32[2 * (i - 1)]) >= thr32;
                 const unsigned bits = __ballot_sync(0xffffffffu, above);
                 if (lane > 0) prev = (bits >> (lane - 1)) & 1u;
-                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev);
+                const int64_t t = t0 + (int64_t)(i - 1);
+                if (carry_here && t == a.nwin - 1) a.carry_out[(int64_t)trial * a.nw + k] = above;
+                const bool keep = t < a.nwin && !(cin && t == 0);
+                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev && keep);
                 if (lane == 0) run_starts[warp][j] = starts;
                 any |= starts;
             }
@@ -594,7 +606,9 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
                 if (lane == 0 && valid && t > 0) prev = box64(t - 1) >= thr_k;
                 const unsigned bits = __ballot_sync(0xffffffffu, above);
                 if (lane > 0) prev = (bits >> (lane - 1)) & 1u;
-                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev);
+                if (carry_here && t == a.nwin - 1) a.carry_out[(int64_t)trial * a.nw + k] = above;
+                const bool keep = t < a.nwin && !(cin && t == 0);
+                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev && keep);
                 if (lane == 0) run_starts[warp][j] = starts;
                 any |= starts;
             }

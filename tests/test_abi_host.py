@@ -109,3 +109,31 @@ def test_workspace_sizes():
         with pytest.raises(hp.HPError) as e:
             p.workspace_bytes(p.max_delay + int(w.widths[-1]))
         assert e.value.code == hp.HP_ERR_NSAMPS_TOO_SHORT
+
+
+@pytest.mark.parametrize("kw", [dict(nbeams=0), dict(nbeams=hp.HP_STREAM_MAX_BEAMS + 1),
+                                dict(gulp=32), dict(max_batch=-1), dict(max_batch=33),
+                                dict(hbm_budget=-5), dict(cand_capacity=0),
+                                dict(raw_capacity=100)])
+def test_stream_rejects_bad_config(kw):
+    # argument checks come before any CUDA call, so they run without a GPU
+    w = workloads.tiny()
+    o = w.obs
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    args = dict(nbeams=2, gulp=4096)
+    args.update(kw)
+    with pytest.raises(hp.HPError) as e:
+        hp.Stream(plan, **args)
+    assert e.value.code == hp.HP_ERR_INVALID_ARG
+
+
+def test_stream_null_arguments():
+    import ctypes as C
+    L = hp.lib()
+    assert L.hp_stream_open(None, None, None) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_stream_push(None, 0, None, 0) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_stream_end_beam(None, 0) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_stream_get_stats(None, None) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_stream_close(None) == hp.HP_OK
+    h = C.c_void_p()
+    assert L.hp_stream_open(C.byref(h), None, None) == hp.HP_ERR_INVALID_ARG and not h.value
