@@ -121,11 +121,11 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_T_GAP 3          /* merge: max gap between boxcar windows, samples */
 #define HP_PARAM_W_TOL 4          /* merge: max |width index difference| (>= 0) */
 #define HP_PARAM_RAW_CAPACITY 5   /* raw-candidate scratch capacity (>= 1024) */
-#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1) */
+#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 22 */
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
 
-#define HP_NUM_DEDISP_CONFIGS 17
+#define HP_NUM_DEDISP_CONFIGS 24
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);

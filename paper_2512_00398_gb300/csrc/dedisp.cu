@@ -38,6 +38,13 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
     {2, 7, 12, 1, 36 * 1024, 1, 2, 6}, // byte rows: 12+1 warps, BD 24, BT 896, 6 buffers
     {2, 7, 6, 2, 36 * 1024, 1, 2, 6},  // byte rows: 12+1 warps, BD 12, BT 1792, 6 buffers
     {2, 5, 12, 1, 36 * 1024, 1, 2, 6}, // byte rows: 12+1 warps, BD 24, BT 640, 6 buffers
+    {2, 5, 8, 2, 54 * 1024, 1, 2, 4},  // byte rows: 16+1 warps, BD 16, BT 1280, 4 x 54 KB
+    {2, 5, 8, 2, 27 * 1024, 1, 2, 8},  // byte rows: 16+1 warps, BD 16, BT 1280, 8 x 27 KB
+    {2, 5, 8, 2, 72 * 1024, 1, 2, 3},  // byte rows: 16+1 warps, BD 16, BT 1280, 3 x 72 KB
+    {2, 7, 12, 1, 54 * 1024, 1, 2, 4}, // byte rows: 12+1 warps, BD 24, BT 896, 4 x 54 KB
+    {2, 5, 12, 1, 54 * 1024, 1, 2, 4}, // byte rows: 12+1 warps, BD 24, BT 640, 4 x 54 KB
+    {2, 7, 12, 1, 54 * 1024, 1, 2, 4}, // as 20, channel-pair loop unrolled twice
+    {2, 5, 8, 2, 72 * 1024, 1, 2, 3},  // as 19, channel-pair loop unrolled twice
 };
 
 namespace {
@@ -830,7 +837,7 @@ __device__ __forceinline__ uint32_t imad_add(uint32_t acc, uint32_t x, uint32_t 
     return r;
 }
 
-template <int RD, int NW, int WD, int WT, int NB>
+template <int RD, int NW, int WD, int WT, int NB, int UNR = 1>
 __global__ void __launch_bounds__(32 * (WD * WT + 1), 1)
 dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, int* status,
                    uint64_t timeout_ns, uint32_t one) {
@@ -924,38 +931,37 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
             return;
         const uint32_t B = sbase + (uint32_t)(b * stage_bytes);
         const StageDesc S = J.stages[T.stage_begin + s];
-        const uint32_t tab = B + S.addr_off + (uint32_t)(wd * RD * 16);
+        uint32_t tab = B + S.addr_off + (uint32_t)(wd * RD * 16);
         const uint32_t tb = B + lane_off;
         const uint32_t nchan = S.nchan;
-        for (uint32_t c = 0; c < nchan; c += 2) {
-            const bool two = c + 1 < nchan;
+        // one channel of trial r: NW + 1 row words at byte address a, aligned by
+        // selector sel and added into the trial's 16-bit lanes
+        auto add_row = [&](int r, uint32_t a, uint32_t sel) {
+            uint32_t w[NW + 1];
+#pragma unroll
+            for (int i = 0; i <= NW; ++i) w[i] = lds32(a + 4 * i);
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                const uint32_t v = __byte_perm(w[i], w[i + 1], sel);
+                acc_lo[r][i] = imad_add(acc_lo[r][i], __byte_perm(v, 0, 0x4240), one);
+                acc_hi[r][i] = imad_add(acc_hi[r][i], __byte_perm(v, 0, 0x4341), one);
+            }
+        };
+        // channel pairs: table entry {offset ch0, offset ch1, selector ch0, selector ch1}
+#pragma unroll UNR
+        for (uint32_t pr = nchan >> 1; pr > 0; --pr, tab += BD * 16) {
 #pragma unroll
             for (int r = 0; r < RD; ++r) {
-                // {offset ch0, offset ch1, selector ch0, selector ch1}
-                const uint4 e = lds128(tab + (c >> 1) * (BD * 16) + r * 16);
-                const uint32_t a0 = tb + e.x, a1 = tb + e.y;
-                const uint32_t s0 = e.z, s1 = e.w;
-                uint32_t w0[NW + 1], w1[NW + 1];
+                const uint4 e = lds128(tab + r * 16);
+                add_row(r, tb + e.x, e.z);
+                add_row(r, tb + e.y, e.w);
+            }
+        }
+        if (nchan & 1) {   // the odd last channel (its pair entry repeats it as ch1)
 #pragma unroll
-                for (int i = 0; i <= NW; ++i) w0[i] = lds32(a0 + 4 * i);
-                if (two) {
-#pragma unroll
-                    for (int i = 0; i <= NW; ++i) w1[i] = lds32(a1 + 4 * i);
-                }
-#pragma unroll
-                for (int i = 0; i < NW; ++i) {
-                    const uint32_t v0 = __byte_perm(w0[i], w0[i + 1], s0);
-                    acc_lo[r][i] = imad_add(acc_lo[r][i], __byte_perm(v0, 0, 0x4240), one);
-                    acc_hi[r][i] = imad_add(acc_hi[r][i], __byte_perm(v0, 0, 0x4341), one);
-                }
-                if (two) {
-#pragma unroll
-                    for (int i = 0; i < NW; ++i) {
-                        const uint32_t v1 = __byte_perm(w1[i], w1[i + 1], s1);
-                        acc_lo[r][i] = imad_add(acc_lo[r][i], __byte_perm(v1, 0, 0x4240), one);
-                        acc_hi[r][i] = imad_add(acc_hi[r][i], __byte_perm(v1, 0, 0x4341), one);
-                    }
-                }
+            for (int r = 0; r < RD; ++r) {
+                const uint4 e = lds128(tab + r * 16);
+                add_row(r, tb + e.x, e.z);
             }
         }
         __syncwarp();
@@ -999,13 +1005,13 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
     }
 }
 
-template <int RD, int NW, int WD, int WT, int NB>
+template <int RD, int NW, int WD, int WT, int NB, int UNR = 1>
 cudaError_t run_dedisp_rows(const DedispBatch& b, int stage_bytes, int* status,
                             uint64_t timeout_ns, cudaStream_t s) {
     const int64_t total = b.prefix[b.njobs];
     if (total <= 0) return cudaSuccess;
     const size_t smem = (size_t)NB * stage_bytes + 2 * NB * 8;
-    auto k = dedisp_rows_kernel<RD, NW, WD, WT, NB>;
+    auto k = dedisp_rows_kernel<RD, NW, WD, WT, NB, UNR>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)total, 32 * (WD * WT + 1), smem, s>>>(b, stage_bytes, status, timeout_ns, 1u);
@@ -1082,6 +1088,13 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
         case 14: return run_dedisp_rows<2, 7, 12, 1, 6>(b, sb, status, timeout_ns, s);
         case 15: return run_dedisp_rows<2, 7, 6, 2, 6>(b, sb, status, timeout_ns, s);
         case 16: return run_dedisp_rows<2, 5, 12, 1, 6>(b, sb, status, timeout_ns, s);
+        case 17: return run_dedisp_rows<2, 5, 8, 2, 4>(b, sb, status, timeout_ns, s);
+        case 18: return run_dedisp_rows<2, 5, 8, 2, 8>(b, sb, status, timeout_ns, s);
+        case 19: return run_dedisp_rows<2, 5, 8, 2, 3>(b, sb, status, timeout_ns, s);
+        case 20: return run_dedisp_rows<2, 7, 12, 1, 4>(b, sb, status, timeout_ns, s);
+        case 21: return run_dedisp_rows<2, 5, 12, 1, 4>(b, sb, status, timeout_ns, s);
+        case 22: return run_dedisp_rows<2, 7, 12, 1, 4, 2>(b, sb, status, timeout_ns, s);
+        case 23: return run_dedisp_rows<2, 5, 8, 2, 3, 2>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

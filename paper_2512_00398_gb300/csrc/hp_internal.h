@@ -44,7 +44,7 @@ struct DedispConfig {
     int BT() const { return WT * NW * (layout == 1 ? 64 : 128); }
     int threads() const { return 32 * WD * WT; }
 };
-constexpr int kNumDedispConfigs = 17;
+constexpr int kNumDedispConfigs = 24;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
 
 // One staged channel row of a DM tile (16 bytes, copied into shared memory).

@@ -563,7 +563,7 @@ int time_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, cudaStream_t s, i
 // ================================================================ batching
 struct hp_batch {
     std::vector<hp_plan*> plans;
-    int cfg = 10;
+    int cfg = 22;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> done;
     cudaEvent_t fork = nullptr;

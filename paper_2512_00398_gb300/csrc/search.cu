@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
     extern __shared__ int64_t P[];   // P[i] = sum of y over samples [base, base + i)
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t warp_max[32];
-    __shared__ unsigned run_starts[kDetectThreads / 32][kDetectPer];
+    __shared__ unsigned above_bits[kDetectThreads / 32][kDetectPer];
     const int trial = blockIdx.y;
     const int64_t n = a.nout;
     const int64_t t0 = (int64_t)blockIdx.x * kDetectTile;
@@ -566,51 +566,38 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
         const int Wi = (int)W;
         const int64_t last = n - W;                     // last valid boxcar start
         const int64_t tend = min(t0 + kDetectTile, last + 1);
-        if (carry_here && tid == 0 && a.nwin - 1 >= tend)   // start nwin - 1 not valid
-            a.carry_out[(int64_t)trial * a.nw + k] = 0;
-        if (t0 >= tend) continue;
-        const int32_t thr32 = (int32_t)min(thr_k, (int64_t)INT32_MAX);
         auto box64 = [&](int64_t u) { return P[u - base + W] - P[u - base]; };
         auto box32 = [&](int64_t u) {
             const int i = (int)(u - base);
             return (int64_t)(int32_t)(P32[2 * (i + Wi)] - P32[2 * i]);
         };
+        if (carry_here && tid == 0)    // is start nwin - 1 above threshold?
+            a.carry_out[(int64_t)trial * a.nw + k] =
+                a.nwin - 1 < tend && box64(a.nwin - 1) >= thr_k;
+        if (t0 >= tend) continue;
+        const int32_t thr32 = (int32_t)min(thr_k, (int64_t)INT32_MAX);
+        const bool full = t0 + kDetectTile <= tend;     // every start of the tile is valid
+        // hot loop: only the above-threshold mask of each warp-wide group of
+        // starts (runs are rare; their starts are found below)
         unsigned any = 0;
         if (narrow) {
 #pragma unroll
             for (int j = 0; j < kDetectPer; ++j) {
-                // warp-consecutive starts; a start opens a run if its left
-                // neighbour (the previous lane, or for lane 0 computed here) is below
                 const int i = i_first + j * kDetectThreads;
-                const bool valid = t0 + (int64_t)(i - 1) < tend;
-                const bool above = valid && (int32_t)(P32[2 * (i + Wi)] - pr[j]) >= thr32;
-                bool prev = false;
-                if (lane == 0 && valid && t0 + (int64_t)(i - 1) > 0)
-                    prev = (int32_t)(P32[2 * (i - 1 + Wi)] - P32[2 * (i - 1)]) >= thr32;
+                bool above = (int32_t)(P32[2 * (i + Wi)] - pr[j]) >= thr32;
+                if (!full) above = above && t0 + (int64_t)(i - 1) < tend;
                 const unsigned bits = __ballot_sync(0xffffffffu, above);
-                if (lane > 0) prev = (bits >> (lane - 1)) & 1u;
-                const int64_t t = t0 + (int64_t)(i - 1);
-                if (carry_here && t == a.nwin - 1) a.carry_out[(int64_t)trial * a.nw + k] = above;
-                const bool keep = t < a.nwin && !(cin && t == 0);
-                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev && keep);
-                if (lane == 0) run_starts[warp][j] = starts;
-                any |= starts;
+                if (lane == 0) above_bits[warp][j] = bits;
+                any |= bits;
             }
         } else {
 #pragma unroll 1
             for (int j = 0; j < kDetectPer; ++j) {
                 const int64_t t = t0 + (int64_t)j * kDetectThreads + tid;
-                const bool valid = t < tend;
-                const bool above = valid && box64(t) >= thr_k;
-                bool prev = false;
-                if (lane == 0 && valid && t > 0) prev = box64(t - 1) >= thr_k;
+                const bool above = t < tend && box64(t) >= thr_k;
                 const unsigned bits = __ballot_sync(0xffffffffu, above);
-                if (lane > 0) prev = (bits >> (lane - 1)) & 1u;
-                if (carry_here && t == a.nwin - 1) a.carry_out[(int64_t)trial * a.nw + k] = above;
-                const bool keep = t < a.nwin && !(cin && t == 0);
-                const unsigned starts = __ballot_sync(0xffffffffu, above && !prev && keep);
-                if (lane == 0) run_starts[warp][j] = starts;
-                any |= starts;
+                if (lane == 0) above_bits[warp][j] = bits;
+                any |= bits;
             }
         }
         if (!any) continue;
@@ -618,8 +605,17 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
         // runs are rare: follow each with the whole warp outside the unrolled loop
 #pragma unroll 1
         for (int j = 0; j < kDetectPer; ++j) {
-            unsigned starts = run_starts[warp][j];
+            const unsigned bits = above_bits[warp][j];
+            if (!bits) continue;
             const int64_t tg = t0 + (int64_t)j * kDetectThreads + warp * 32;   // group base
+            // a start opens a run when its left neighbour is below threshold (for
+            // lane 0 the neighbour is start tg - 1 of the group before)
+            const bool left = tg > 0 && (narrow ? box32(tg - 1) : box64(tg - 1)) >= thr_k;
+            unsigned starts = bits & ~((bits << 1) | (left ? 1u : 0u));
+            // streamed search: runs must begin inside the window [0, nwin), and a
+            // run at start 0 that the previous gulp left open is not reported again
+            if (a.nwin < tg + 32) starts &= a.nwin <= tg ? 0u : (1u << (int)(a.nwin - tg)) - 1u;
+            if (cin && tg == 0) starts &= ~1u;
             while (starts) {
                 const int L = __ffs(starts) - 1;
                 starts &= starts - 1;

@@ -83,7 +83,7 @@ def test_params_roundtrip_and_validation():
     o = w.obs
     with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
         assert p.get_param("w_tol") == w.nw
-        assert p.get_param("dedisp_config") == 10
+        assert p.get_param("dedisp_config") == 22
         for name, val in [("baseline_mode", 1), ("baseline_s", 0.5), ("dm_tol", 3), ("t_gap", -2),
                           ("w_tol", 1), ("raw_capacity", 4096), ("dedisp_config", 3),
                           ("stage_timing", 1), ("timeout_s", 0.25)]:
