@@ -32,13 +32,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DM-trial·samples/s"
 
-# DRAM traffic of the dedispersion kernel from the last ncu capture
-# (profiles/dedisp_kernel_fast_4096ch.md): read + write bytes per launch divided by
-# the output samples per trial of the captured case (the traffic grows with the
-# number of time tiles).  Keyed by the kernel source it was measured on; a changed
-# kernel reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "83dd9a408eae2429", "bytes_per_output_sample": 7.330154e9 / 37556,
-                  "ndm": 1500, "nchans": 4096}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dedispersion kernel on this exact workload and tile configuration, from a one-pass ncu
+# capture of the full-size bench command (profiles/dedisp_rows_kernel_fast_4096ch.md).
+# Keyed by the kernel source it was measured on; a changed kernel, another workload or
+# another configuration reports null until it is captured again.
+DEDISP_TRAFFIC = {"source_sha256_16": "fcdc92af36704ea1", "bytes": 37.77e9 + 5.74e9,
+                  "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22}
 
 
 def parse():
@@ -145,14 +145,23 @@ def describe(w, nout):
             "nout": nout, "nw": w.nw, "l2": "inputs larger than L2 (no flush)"}
 
 
-def dedisp_traffic(w, nout):
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0   # earlier GB300 measurement, used only when the file is absent
+
+
+def dedisp_traffic(w, config):
     import hashlib
     src = os.path.join(ROOT, "paper_2512_00398_gb300", "csrc", "dedisp.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     t = DEDISP_TRAFFIC
-    if sha != t["source_sha256_16"] or w.ndm != t["ndm"] or w.obs.nchans != t["nchans"]:
+    if (sha != t["source_sha256_16"] or w.ndm != t["ndm"] or w.obs.nchans != t["nchans"]
+            or w.obs.nsamps != t["nsamps"] or config != t["config"]):
         return None
-    return t["bytes_per_output_sample"] * nout
+    return t["bytes"]
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -297,12 +306,24 @@ def run_ours(args):
         # operation, so the add peak is twice the measured 32-bit add issue rate
         peak_adds = 2.0 * peaks["int_add_ops_per_s"]
         achieved = adds / (dd_ms * 1e-3)
+        cfg = int(plan.get_param("dedisp_config"))
+        traffic = dedisp_traffic(w, cfg)
+        alg_bytes = float(o.nchans) * o.nsamps + 4.0 * w.ndm * nout
+        hbm_peak = measured_hbm_gbs()
         line["roofline"] = {
-            "bound": "alu", "kernel": "dedisp_kernel", "achieved": achieved / 1e12,
+            "bound": "alu", "kernel": "dedisp_rows_kernel", "achieved": achieved / 1e12,
             "peak": peak_adds / 1e12, "unit": "Tadd/s", "frac": achieved / peak_adds,
-            "traffic": dedisp_traffic(w, nout),
+            "traffic": traffic,
             "algorithmic": f"{w.ndm} trials x {o.nchans} ch x {nout} samples = {adds:.3e} "
-                           f"byte-adds per launch",
+                           f"byte-adds per launch; {alg_bytes:.3e} algorithmic bytes (input "
+                           f"once + int32 output)",
+            "traffic_over_algorithmic": traffic / alg_bytes if traffic else None,
+            "hbm": {"achieved_gbs": traffic / (dd_ms * 1e-3) / 1e9 if traffic else None,
+                    "peak_gbs": hbm_peak, "basis": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            # each 4-sample word costs three ALU-pipe ops (align + two splits); the
+            # measured PRMT rate is the ALU pipe's rate
+            "frac_vs_alu_design_ceiling": achieved / (peaks["prmt_ops_per_s"] * 4.0 / 3.0),
+            "config": cfg,
             "peak_basis": "measured int32 add issue rate x 2 (16-bit SWAR lanes); "
                           f"int32 {peaks['int_add_ops_per_s'] / 1e12:.2f} Tops/s, PRMT "
                           f"{peaks['prmt_ops_per_s'] / 1e12:.2f} Tops/s, LDS.32 "

@@ -831,6 +831,8 @@ cudaError_t run_dedisp16(const DedispBatch& b, int stage_bytes, int* status, uin
 // into two 16-bit lanes with two more; the lanes are summed with IMADs by a
 // runtime 1, which keeps the adds on the FMA pipe while the PRMTs use the ALU
 // pipe.  No block-wide barrier after set-up; every wait is bounded.
+constexpr int kTimeGroup = 16;   // time tiles per block group (byte-row kernel)
+
 __device__ __forceinline__ uint32_t imad_add(uint32_t acc, uint32_t x, uint32_t one) {
     uint32_t r;
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(one), "r"(acc));
@@ -856,8 +858,16 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
     while (jb + 1 < batch.njobs && batch.prefix[jb + 1] <= blk) ++jb;
     const DedispJob& J = batch.jobs[jb];
     const int64_t item = blk - batch.prefix[jb];
-    const int tt = (int)(item % J.ntt);
-    const int dt = (int)(item / J.ntt);
+    // Blocks in groups of kTimeGroup time tiles, every DM tile of a group before
+    // the next group: the blocks resident together read neighbouring windows of
+    // the same channel rows, which L2 then serves (DM-tile-major order re-reads
+    // the whole input from DRAM once per DM tile).
+    const int64_t per = (int64_t)kTimeGroup * J.ndt;
+    const int64_t grp = item / per;
+    const int64_t rem = item - grp * per;
+    const int64_t gsz = min((int64_t)kTimeGroup, (int64_t)J.ntt - grp * kTimeGroup);
+    const int dt = (int)(rem / gsz);
+    const int tt = (int)(grp * kTimeGroup + rem % gsz);
     const TileDesc T = J.tiles[dt];
     const int64_t t0 = (int64_t)tt * BT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
