@@ -249,20 +249,44 @@ def run_ours(args):
     stats = hp.hp_plan_stats(plan, reset=True)
     plan.set_param("stage_timing", 0)
 
-    # end to end through the public call: pinned host input -> device, search,
-    # device -> host read of the count and the candidate records
+    # end to end through the public call: every step copies its 4.3 GB input from
+    # pinned host memory to the device, searches it and reads the count and the
+    # candidate records back.  Two device input buffers: the copy of the next
+    # step's input (on a copy stream) overlaps this step's search; the timed
+    # region holds exactly `steps` copies, searches and reads (the copy for the
+    # first timed step is issued before it, one for the step after the last inside).
     e2e = None
     if not args.no_e2e:
         host = torch.from_numpy(s.data).pin_memory()
         res = torch.empty(out[0].numel(), dtype=torch.uint8).pin_memory()
         cnt_h = torch.empty(1, dtype=torch.int64).pin_memory()
+        bufs = [fb, torch.empty_like(fb)]
+        cs = torch.cuda.Stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        used = [torch.cuda.Event(), torch.cuda.Event()]
+        used_rec = [False, False]
+
+        def upload(k):
+            b = k % 2
+            if used_rec[b]:
+                cs.wait_event(used[b])       # the search that last read this buffer
+            with torch.cuda.stream(cs):
+                bufs[b].copy_(host, non_blocking=True)
+            copied[b].record(cs)
+
+        upload(0)
         d2h = []
-        for it in range(args.warmup + args.steps):
+        total = args.warmup + args.steps
+        for it in range(total):
             if it == args.warmup:
                 barrier()
                 t0 = time.perf_counter()
-            fb.copy_(host, non_blocking=True)
-            hp.hp_search(plan, fb, stream, out=out)
+            b = it % 2
+            stream.wait_event(copied[b])
+            hp.hp_search(plan, bufs[b], stream, out=out)
+            used[b].record(stream)
+            used_rec[b] = True
+            upload(it + 1)
             cnt_h.copy_(out[1], non_blocking=True)
             stream.synchronize()
             n = min(int(cnt_h.item()), out[0].numel() // hp.CAND_DTYPE.itemsize)
@@ -272,9 +296,11 @@ def run_ours(args):
             stream.synchronize()
             if it >= args.warmup:
                 d2h.append(8 + nb)
+        cs.synchronize()
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
         e2e = [e2e_s, float(np.mean(d2h))]
+        del bufs
 
     # max over ranks
     vals = torch.tensor([dev_ms, e2e[0] if e2e else 0.0], dtype=torch.float64, device="cuda")
@@ -335,7 +361,9 @@ def run_ours(args):
         if e2e:
             line["e2e"] = {"value": world * units / e2e_s, "unit": METRIC,
                            "h2d_bytes_per_step": int(s.data.nbytes), "d2h_bytes_per_step": int(e2e[1]),
-                           "ms_per_step": e2e_s * 1e3}
+                           "ms_per_step": e2e_s * 1e3,
+                           "copies": "pinned host -> device every step, overlapped with the "
+                                     "previous step's search (two input buffers)"}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s, w)
     if world == 1 and not args.no_batch:

@@ -149,7 +149,7 @@ struct TailRec {
     int64_t S_prev;   // S at u - 1 (above threshold)
     int64_t best_S, best_t;
 };
-constexpr int64_t kTailCap = 1 << 16;
+constexpr int64_t kTailCap = 1 << 20;
 
 struct SearchArgs {
     const int32_t* D;          // [ndm][pitch]

@@ -239,6 +239,44 @@ def test_fast_full_size_sampled(hp, torch, fast_full):
     assert (got["t_lo"] <= got["sample"]).all() and (got["sample"] < got["t_hi"]).all()
 
 
+def test_stress_full_size_sampled(hp, torch):
+    """The stress shape (4096 ch x 2^21 samples, ~4000 trials on DM 0-5000,
+    boxcars 1..8192) with zero-DM spikes, narrowband tones and a baseline
+    drift: sampled dedispersed sums exact, and on sampled trials (including
+    DM 0, where the broadband spikes add up) baseline, sigma and the raw
+    candidates equal the oracle's."""
+    from paper_2512_00398_gb300 import workloads
+    w = workloads.stress()
+    s = w.generate(threads=16)
+    o = w.obs
+    fb = torch.from_numpy(s.data).cuda()
+    # the drift leaves long-boxcar residuals above threshold at every DM:
+    # ~17 000 raw candidates per trial, ~6e7 in all
+    p = _plan(hp, w, raw_capacity=1 << 26)
+    tab = p.delays()
+    nout = p.nout(fb.shape[0])
+    D = hp.hp_dedisperse(p, fb)
+    assert hp.hp_plan_sync_status(p) == hp.HP_OK
+    rng = np.random.default_rng(23)
+    ds = rng.integers(0, w.ndm, 100)
+    ts = rng.integers(0, nout, 100)
+    ts[:4] = [0, nout - 1, nout - 2, 895]
+    Dh = D[torch.from_numpy(ds).cuda(), torch.from_numpy(ts).cuda()].cpu().numpy()
+    for d, t, v in zip(ds, ts, Dh):
+        assert oracle.dedisperse_point(s.data, tab[d], int(t)) == int(v), (d, t)
+    raw_g, sig_g, mad_g = hp.detect(p, D, nout, capacity=1 << 26)
+    assert raw_g.size > 0
+    for d in [0, 1, int(w.ndm // 3), w.ndm - 1]:
+        Do = oracle.dedisperse(s.data, tab, rows=(d, d + 1))
+        assert np.array_equal(Do[0], D[d, :nout].cpu().numpy())
+        raw_o, sig_o, mad_o = oracle.search_trials(Do, d, o.tsamp, w.widths, w.threshold)
+        assert mad_g[d] == mad_o[0] and sig_g[d] == sig_o[0]
+        assert _key(raw_g[raw_g["dm_idx"] == d]) == _key(raw_o)
+    del D
+    got = hp.search(p, fb, capacity=1 << 24)
+    assert int(got["members"].sum()) == raw_g.size
+
+
 def test_fast_full_size_recovery(hp, torch, fast_full):
     from tests.test_oracle_pins import recovered
     w, s, fb = fast_full
