@@ -125,7 +125,7 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
 
-#define HP_NUM_DEDISP_CONFIGS 24
+#define HP_NUM_DEDISP_CONFIGS 27
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);
@@ -173,7 +173,8 @@ int hp_dedisperse(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps,
 
 /* The per-trial stages (baseline removal, normalisation, matched filtering,
  * peak detection; Algorithm 1's trial loop) on dedispersed series:
- *   series_dev  device int32 [ndm][pitch], nout valid samples per row
+ *   series_dev  device int32 [ndm][pitch], nout valid samples per row, values
+ *               within +-2^30 (y = D - b is kept as int32); left unchanged
  *   raw_out     caller-owned raw-candidate buffer (count = true number)
  *   sigma_dev   optional device double [ndm]: per-trial sigma (NULL to skip)
  *   mad_dev     optional device int64 [ndm]: per-trial median |y| (NULL to skip) */

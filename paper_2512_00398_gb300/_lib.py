@@ -31,7 +31,7 @@ HP_PARAM_RAW_CAPACITY = 5
 HP_PARAM_DEDISP_CONFIG = 6
 HP_PARAM_STAGE_TIMING = 7
 HP_PARAM_TIMEOUT_S = 8
-HP_NUM_DEDISP_CONFIGS = 24
+HP_NUM_DEDISP_CONFIGS = 27
 
 HP_STAGE_TRANSPOSE, HP_STAGE_DEDISP, HP_STAGE_SEARCH, HP_STAGE_MERGE = 0, 1, 2, 3
 HP_NUM_STAGES = 4

@@ -59,19 +59,26 @@ def _compile(src: str, extra) -> str:
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile (if stale) and return the path of the shared library."""
+    """Compile (if stale) and return the path of the shared library.  Concurrent
+    callers (test workers) serialise on a lock file; the library is replaced
+    atomically."""
     if not force and not is_stale():
         return LIB
+    import fcntl
     os.makedirs(OUT_DIR, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with open(os.path.join(OUT_DIR, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not is_stale():   # another process built it meanwhile
+            return LIB
+        extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+        with ThreadPoolExecutor(len(SOURCES)) as ex:
+            objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
+        tmp = LIB + f".{os.getpid()}.tmp"
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
     return LIB
 
 

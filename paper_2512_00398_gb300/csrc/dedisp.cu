@@ -45,6 +45,9 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
     {2, 5, 12, 1, 54 * 1024, 1, 2, 4}, // byte rows: 12+1 warps, BD 24, BT 640, 4 x 54 KB
     {2, 7, 12, 1, 54 * 1024, 1, 2, 4}, // as 20, channel-pair loop unrolled twice
     {2, 5, 8, 2, 72 * 1024, 1, 2, 3},  // as 19, channel-pair loop unrolled twice
+    {1, 7, 24, 1, 54 * 1024, 1, 2, 4}, // 24+1 warps, 1 trial per warp, BD 24, BT 896
+    {1, 5, 30, 1, 54 * 1024, 1, 2, 4}, // 30+1 warps, 1 trial per warp, BD 30, BT 640
+    {1, 7, 16, 1, 54 * 1024, 1, 2, 4}, // 16+1 warps, 1 trial per warp, BD 16, BT 896
 };
 
 namespace {
@@ -1105,6 +1108,9 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
         case 21: return run_dedisp_rows<2, 5, 12, 1, 4>(b, sb, status, timeout_ns, s);
         case 22: return run_dedisp_rows<2, 7, 12, 1, 4, 2>(b, sb, status, timeout_ns, s);
         case 23: return run_dedisp_rows<2, 5, 8, 2, 3, 2>(b, sb, status, timeout_ns, s);
+        case 24: return run_dedisp_rows<1, 7, 24, 1, 4, 2>(b, sb, status, timeout_ns, s);
+        case 25: return run_dedisp_rows<1, 5, 30, 1, 4, 2>(b, sb, status, timeout_ns, s);
+        case 26: return run_dedisp_rows<1, 7, 16, 1, 4, 2>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

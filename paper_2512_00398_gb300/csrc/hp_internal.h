@@ -44,7 +44,7 @@ struct DedispConfig {
     int BT() const { return WT * NW * (layout == 1 ? 64 : 128); }
     int threads() const { return 32 * WD * WT; }
 };
-constexpr int kNumDedispConfigs = 24;
+constexpr int kNumDedispConfigs = 27;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
 
 // One staged channel row of a DM tile (16 bytes, copied into shared memory).
@@ -174,6 +174,8 @@ struct SearchArgs {
     int64_t* mad;              // [ndm]
     double* sigma;             // [ndm]
     int64_t* tint;             // [ndm][nw] integer thresholds
+    int32_t* Y;                // [ndm][ypitch] baseline-subtracted series y = D - b, written
+    int64_t ypitch;            // by the histogram pass (may alias D in median mode)
     hp_raw_cand* raw;          // output
     int64_t raw_cap;
     int64_t* raw_count;

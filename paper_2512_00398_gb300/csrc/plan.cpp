@@ -278,6 +278,15 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
         L.D = take((size_t)ndm * L.dpitch * 4);
     }
     L.search_begin = off;
+    // y = D - b: written over the plan's own dedispersed series in median mode
+    // (whose baseline reads only the remedian knots); a separate array in mean
+    // mode (the moving window reads D around each sample) and for a caller's
+    // series (hp_detect leaves it unchanged)
+    L.y_in_D = with_dedisp && p->baseline_mode == 0;
+    if (!L.y_in_D) {
+        L.ypitch = round_up64(std::max<int64_t>(L.nout, 1), 64);
+        L.y = take((size_t)ndm * L.ypitch * 4);
+    }
     // remedian passes of up to five levels: pass 1 writes buffer a, pass 2
     // buffer b, later passes alternate (each pass shrinks the series)
     const int levels = remedian_levels(baseline_window(p));
@@ -482,6 +491,13 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.tail_cap = kTailCap;
     a.tail_count = (int64_t*)(ws + L.tcount);
     a.status = p->status;
+    if (L.y_in_D) {
+        a.Y = const_cast<int32_t*>(D);
+        a.ypitch = pitch;
+    } else {
+        a.Y = (int32_t*)(ws + L.y);
+        a.ypitch = L.ypitch;
+    }
     a.nwin = nout;
     a.carry_in = nullptr;
     a.carry_out = nullptr;

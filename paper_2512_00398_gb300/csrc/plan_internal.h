@@ -22,6 +22,9 @@ struct Layout {
            mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
            vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
            dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
+    size_t y = 0;              // baseline-subtracted series (unless it overwrites D)
+    int64_t ypitch = 0;
+    bool y_in_D = false;
     size_t total = 0;
     size_t search_begin = 0;   // everything from here on is search/merge scratch
 };

@@ -246,15 +246,20 @@ __device__ __forceinline__ void load_chunk32(const int32_t* __restrict__ row, in
     }
 }
 
+// Histogram of |y| per trial; also writes y = D - b (int32: |D|, |b| < 2^21)
+// for the passes after it.  Each thread reads its whole chunk before it
+// writes, so Y may alias D (median mode, whose walker reads only the knots).
 template <int MODE>
-__global__ void __launch_bounds__(256) mad_hist_kernel(const int32_t* __restrict__ D,
-                                                       int64_t pitch, int64_t n, BaselineCtx bc,
-                                                       int vec, uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(256) mad_hist_kernel(const int32_t* D, int64_t pitch, int64_t n,
+                                                       BaselineCtx bc, int vec,
+                                                       uint32_t* __restrict__ hist, int32_t* Y,
+                                                       int64_t ypitch, int yvec) {
     __shared__ uint32_t h[kHistBins];
     const int trial = blockIdx.y;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const int32_t* row = D + (int64_t)trial * pitch;
+    int32_t* yrow = Y + (int64_t)trial * ypitch;
     const int64_t t_begin = (int64_t)blockIdx.x * kHistChunk + threadIdx.x * 32;
     const int64_t t_end = min(n, t_begin + 32);
     if (t_begin < t_end) {
@@ -266,11 +271,21 @@ __global__ void __launch_bounds__(256) mad_hist_kernel(const int32_t* __restrict
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             if (t_begin + q < t_end) {
-                int64_t y = (int64_t)v[q] - w.value();
-                if (y < 0) y = -y;
-                atomicAdd(&h[hist_bin(y)], 1u);
+                const int32_t y = (int32_t)((int64_t)v[q] - w.value());
+                v[q] = y;
+                atomicAdd(&h[hist_bin(y < 0 ? -(int64_t)y : (int64_t)y)], 1u);
                 w.step();
             }
+        }
+        if (yvec && t_end - t_begin == 32) {
+            int4* p = reinterpret_cast<int4*>(yrow + t_begin);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                p[q] = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (t_begin + q < t_end) yrow[t_begin + q] = v[q];
         }
     }
     __syncthreads();
@@ -337,10 +352,8 @@ __global__ void __launch_bounds__(1024) mad_select_kernel(uint32_t* __restrict__
         for (int i = threadIdx.x; i < kHistFine; i += blockDim.x) hrow[i] = 0;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) mad_refine_hist_kernel(const int32_t* __restrict__ D,
-                                                              int64_t pitch, int64_t n,
-                                                              BaselineCtx bc, int vec,
+__global__ void __launch_bounds__(256) mad_refine_hist_kernel(const int32_t* __restrict__ Y,
+                                                              int64_t ypitch, int64_t n, int yvec,
                                                               const int32_t* __restrict__ bucket,
                                                               uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kHistFine];
@@ -349,22 +362,17 @@ __global__ void __launch_bounds__(256) mad_refine_hist_kernel(const int32_t* __r
     if (B < 0) return;
     for (int i = threadIdx.x; i < kHistFine; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int32_t* row = D + (int64_t)trial * pitch;
+    const int32_t* yrow = Y + (int64_t)trial * ypitch;
     const int64_t t_begin = (int64_t)blockIdx.x * kHistChunk + threadIdx.x * 32;
     const int64_t t_end = min(n, t_begin + 32);
     if (t_begin < t_end) {
         int32_t v[32];
-        load_chunk32(row, t_begin, t_end, vec != 0, v);
-        Walker<MODE> w;
-        w.setup(bc, row, n, trial);
-        w.init(t_begin);
+        load_chunk32(yrow, t_begin, t_end, yvec != 0, v);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             if (t_begin + q < t_end) {
-                int64_t y = (int64_t)v[q] - w.value();
-                if (y < 0) y = -y;
+                const int64_t y = v[q] < 0 ? -(int64_t)v[q] : (int64_t)v[q];
                 if ((y >> 12) == B) atomicAdd(&h[y & 4095], 1u);
-                w.step();
             }
         }
     }
@@ -487,9 +495,7 @@ __device__ __forceinline__ bool follow_run(int64_t ts, int64_t last, int64_t bas
     return tail;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_constant__ SearchArgs a,
-                                                                BaselineCtx bc) {
+__global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_constant__ SearchArgs a) {
     extern __shared__ int64_t P[];   // P[i] = sum of y over samples [base, base + i)
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t warp_max[32];
@@ -499,31 +505,25 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
     const int64_t t0 = (int64_t)blockIdx.x * kDetectTile;
     const int64_t base = t0 - 1;
     const int64_t len = min((int64_t)kDetectTile + a.wmax, n - base);
-    const int32_t* row = a.D + (int64_t)trial * a.pitch;
+    const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // y over [base, base + len), one contiguous chunk per thread (the exact
-    // baseline walker steps sample by sample; an odd chunk length keeps the
-    // 16 threads of a half-warp on distinct banks), then a block prefix sum
+    // y over [base, base + len) into P[1 ..] with coalesced loads (the slot
+    // before sample 0 holds y = 0), then one contiguous chunk per thread (an odd
+    // chunk length keeps the 16 threads of a half-warp on distinct banks) and a
+    // block prefix sum
+    for (int64_t i = tid; i < len; i += kDetectThreads) {
+        const int64_t s = base + i;
+        P[i + 1] = s < 0 ? 0 : (int64_t)yrow[s];
+    }
+    __syncthreads();
     const int64_t per = ((len + kDetectThreads - 1) / kDetectThreads) | 1;
     const int64_t i0 = min(len, tid * per), i1 = min(len, i0 + per);
     int64_t local = 0, ymax = 0;
-    if (i0 < i1) {
-        Walker<MODE> w;
-        w.setup(bc, row, n, trial);
-        int64_t s = base + i0;
-        if (s < 0) {                       // the slot before sample 0 holds y = 0
-            P[i0 + 1] = 0;
-            ++s;
-        }
-        if (s < base + i1) w.init(s);
-        for (; s < base + i1; ++s) {
-            const int64_t y = (int64_t)row[s] - w.value();
-            P[s - base + 1] = y;
-            local += y;
-            ymax = max(ymax, y < 0 ? -y : y);
-            w.step();
-        }
+    for (int64_t i = i0; i < i1; ++i) {
+        const int64_t y = P[i + 1];
+        local += y;
+        ymax = max(ymax, y < 0 ? -y : y);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ymax = max(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
@@ -652,28 +652,20 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
 
 // Runs that leave the detect tile's halo: continue each one sample at a time
 // from the dedispersed row with exact baseline walkers, then emit it.
-template <int MODE>
-__global__ void tail_kernel(const __grid_constant__ SearchArgs a, BaselineCtx bc) {
+__global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
     const int64_t cnt = min(*a.tail_count, a.tail_cap);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt;
          q += (int64_t)gridDim.x * blockDim.x) {
         const TailRec r = a.tails[q];
         const int64_t n = a.nout;
-        const int32_t* row = a.D + (int64_t)r.trial * a.pitch;
+        const int32_t* yrow = a.Y + (int64_t)r.trial * a.ypitch;
         const int64_t W = a.widths[r.k];
         const int64_t last = n - W;
         const int64_t thr = a.tint[(int64_t)r.trial * a.nw + r.k];
         int64_t best_S = r.best_S, best_t = r.best_t, Sp = r.S_prev;
-        Walker<MODE> wa, wb;                         // y(v-1) leaving, y(v+W-1) entering
-        wa.setup(bc, row, n, r.trial);
-        wb.setup(bc, row, n, r.trial);
-        wa.init(r.u - 1);
-        wb.init(r.u - 1 + W);
         for (int64_t v = r.u; v <= last; ++v) {
-            const int64_t Sv = Sp - ((int64_t)row[v - 1] - wa.value()) +
-                               ((int64_t)row[v - 1 + W] - wb.value());
-            wa.step();
-            wb.step();
+            // y(v-1) leaves the window, y(v+W-1) enters it
+            const int64_t Sv = Sp - (int64_t)yrow[v - 1] + (int64_t)yrow[v - 1 + W];
             if (Sv < thr) break;
             if (Sv > best_S) { best_S = Sv; best_t = v; }
             Sp = Sv;
@@ -692,15 +684,16 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
     const int ndm = a.ndm;
     const dim3 hgrid((unsigned)ceil_div(n, kHistChunk), ndm);
     const int vec = ((a.pitch & 3) == 0) && (((uintptr_t)a.D & 15u) == 0);
+    const int yvec = ((a.ypitch & 3) == 0) && (((uintptr_t)a.Y & 15u) == 0);
     ++*nlaunch;
-    mad_hist_kernel<MODE><<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, vec, a.hist);
+    mad_hist_kernel<MODE><<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, vec, a.hist, a.Y, a.ypitch,
+                                                yvec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
     mad_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, n, a.refine_bucket, a.refine_rank, a.mad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
-    mad_refine_hist_kernel<MODE><<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, vec, a.refine_bucket,
-                                                       a.hist);
+    mad_refine_hist_kernel<<<hgrid, 256, 0, s>>>(a.Y, a.ypitch, n, yvec, a.refine_bucket, a.hist);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
     mad_refine_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, a.refine_bucket, a.refine_rank, a.mad);
@@ -710,15 +703,15 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
                                                               a.sigma, a.tint);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
-    if ((e = cudaFuncSetAttribute(detect_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
     const dim3 dgrid((unsigned)ceil_div(n, kDetectTile), ndm);
     ++*nlaunch;
-    detect_kernel<MODE><<<dgrid, kDetectThreads, smem, s>>>(a, bc);
+    detect_kernel<<<dgrid, kDetectThreads, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
-    tail_kernel<MODE><<<64, 128, 0, s>>>(a, bc);
+    tail_kernel<<<64, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
