@@ -69,6 +69,30 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------- ranks (weak scaling)
+def rank_workload(rank, world, nsamps):
+    """One file per rank: the FAST shape, a different seed on every rank when
+    there are several (the path shards by file, nothing is exchanged)."""
+    if world == 1:
+        return workload(nsamps)
+    from paper_2512_00398_gb300 import workloads
+    return workloads.fast(nsamps=nsamps, seed=2 + rank)
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the time)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def aggregate(world, units_per_rank, seconds):
+    """Whole-job throughput: every rank processed `units_per_rank` in `seconds`."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples (200 ms) of one GPU during the timed region."""
@@ -209,10 +233,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = workload(args.nsamps)
-    if world > 1:   # weak scaling: every rank its own file
-        from paper_2512_00398_gb300 import workloads
-        w = workloads.fast(nsamps=args.nsamps, seed=2 + rank)
+    w = rank_workload(rank, world, args.nsamps)
     s = w.generate(threads=min(16, os.cpu_count() or 8))
     o = w.obs
     plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
@@ -302,15 +323,11 @@ def run_ours(args):
         e2e = [e2e_s, float(np.mean(d2h))]
         del bufs
 
-    # max over ranks
-    vals = torch.tensor([dev_ms, e2e[0] if e2e else 0.0], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    dev_ms, e2e_s = float(vals[0]), float(vals[1])
+    dev_ms, e2e_s = max_over_ranks([dev_ms, e2e[0] if e2e else 0.0], dist, "cuda")
     units = w.ndm * nout
     line = None
     if rank == 0:
-        value = world * units / (dev_ms * 1e-3)
+        value = aggregate(world, units, dev_ms * 1e-3)
         clocks = clk.summary()
         adds = float(w.ndm) * o.nchans * nout
         dd_ms = stats["stage_ms"]["dedisp"] / max(1, stats["stage_calls"]["dedisp"])
