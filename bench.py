@@ -93,6 +93,18 @@ def aggregate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
+def recovery_rates(w, pulses, cands):
+    """Injected pulses found among the merged candidates (the criterion of
+    workloads.recovered), for matched S/N >= 10 and for 6-10."""
+    from paper_2512_00398_gb300.workloads import recovered
+    out = {}
+    for name, lo, hi in (("snr>=10", 10.0, float("inf")), ("snr 6-10", 6.0, 10.0)):
+        sel = [p for p in pulses if lo <= p.snr < hi]
+        found = sum(1 for p in sel if recovered(p, cands, w, snr_min=w.threshold))
+        out[name] = f"{found}/{len(sel)}"
+    return out
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples (200 ms) of one GPU during the timed region."""
@@ -251,6 +263,8 @@ def run_ours(args):
     if st != hp.HP_OK:
         raise hp.HPError(st, "warm-up")
     ncl = int(out[1].item())
+    cands = hp.cands_to_numpy(*out)
+    recovery = recovery_rates(w, s.pulses, cands)
     hp.hp_plan_stats(plan, reset=True)
     plan.set_param("stage_timing", 1)
 
@@ -339,6 +353,7 @@ def run_ours(args):
             "config": describe(w, nout),
             "rtf": world * o.duration / (dev_ms * 1e-3),
             "clusters": ncl,
+            "recovery": recovery,
             "stages_ms": {k: v / max(1, stats["stage_calls"][k])
                           for k, v in stats["stage_ms"].items()},
             "gpu_launches": stats["kernel_launches"],
@@ -373,6 +388,22 @@ def run_ours(args):
                           f"{peaks['lds32_bytes_per_s'] / 1e12:.2f} TB/s, "
                           f"{peaks['sm_count']} SMs",
             "frac_vs_int32_rate": achieved / peaks["int_add_ops_per_s"],
+        }
+        # the per-trial stages: the histogram pass reads D and writes y, the
+        # detect pass reads y (the remedian reads D once more at 1/5 of the
+        # rate it walks); per (trial, sample) nw threshold tests + 1 prefix add
+        se_ms = stats["stage_ms"]["search"] / max(1, stats["stage_calls"]["search"])
+        se_bytes = 4.0 * w.ndm * nout * 3
+        se_ops = float(w.ndm) * nout * (w.nw + 1)
+        line["search_roofline"] = {
+            "bound": "alu", "kernels": "remedian, mad_hist, refine, sigma, detect, tail",
+            "achieved_gbs": se_bytes / (se_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
+            "hbm_frac": se_bytes / (se_ms * 1e-3) / 1e9 / hbm_peak,
+            "achieved_tops": se_ops / (se_ms * 1e-3) / 1e12,
+            "int32_peak_tops": peaks["int_add_ops_per_s"] / 1e12,
+            "alu_frac": se_ops / (se_ms * 1e-3) / peaks["int_add_ops_per_s"],
+            "algorithmic": f"{se_bytes:.3e} B (D read, y written, y read) and {se_ops:.3e} "
+                           f"integer ops ((nw + 1) per trial-sample) per search",
         }
         line["clocks"] = clocks
         if e2e:

@@ -287,6 +287,18 @@ int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_dev, int64_t
                     const double* sigma_dev, const int* boxcar_widths, int nw, int dm_tol,
                     int64_t t_gap, int w_tol, void* stream, hp_cand_buf* cand_out);
 
+/* Device memory of the plan (its tables and, unless a workspace is bound, its
+ * search workspace) from a caller's allocator instead of cudaMalloc/cudaFree,
+ * e.g. a framework's caching allocator.  alloc returns a device pointer
+ * aligned to 256 bytes or NULL; free gets back the pointer and its size.  The
+ * plan synchronises the device before it frees anything, so the memory is idle
+ * when free is called.  Both NULL restores cudaMalloc.  Memory obtained from
+ * the previous allocator is returned to it first.  Not thread-safe with
+ * concurrent calls on the same plan. */
+typedef void* (*hp_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*hp_free_fn)(void* ptr, size_t bytes, void* ctx);
+int hp_plan_set_allocator(hp_plan* plan, hp_alloc_fn alloc, hp_free_fn free_fn, void* ctx);
+
 /* Wait for the plan's enqueued work on `stream` and return (then clear) the
  * first device-side status latched since the last call: HP_OK,
  * HP_ERR_CAND_OVERFLOW or HP_ERR_TIMEOUT.  Synchronises the stream. */

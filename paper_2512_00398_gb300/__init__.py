@@ -68,6 +68,31 @@ class Plan:
             raise HPError(HP_ERR_INVALID_ARG, "plan already destroyed")
         return self._h
 
+    def use_allocator(self, alloc=None, free=None):
+        """Take the plan's device memory from Python callables alloc(nbytes) ->
+        int pointer and free(ptr, nbytes) (both None: cudaMalloc again)."""
+        if (alloc is None) != (free is None):
+            raise HPError(HP_ERR_INVALID_ARG, "alloc and free go together")
+        if alloc is None:
+            a, f = _lib_mod.ALLOC_FN(), _lib_mod.FREE_FN()
+        else:
+            a = _lib_mod.ALLOC_FN(lambda n, ctx: int(alloc(int(n))) or None)
+            f = _lib_mod.FREE_FN(lambda ptr, n, ctx: free(int(ptr), int(n)))
+        check(lib().hp_plan_set_allocator(self.handle, a, f, None), "hp_plan_set_allocator")
+        self._alloc_cbs = (a, f)        # the library calls them until replaced
+
+    def use_torch_allocator(self):
+        """The plan's tables and workspace from torch's caching allocator."""
+        import torch
+
+        def alloc(n):
+            return torch.cuda.caching_allocator_alloc(n)
+
+        def free(ptr, n):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.use_allocator(alloc, free)
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().hp_plan_destroy(self._h)

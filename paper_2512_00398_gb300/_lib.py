@@ -53,7 +53,10 @@ EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_pa
            "hp_plan_autotune", "hp_batch_create", "hp_batch_destroy", "hp_batch_set_config",
            "hp_batch_autotune", "hp_batch_search", "hp_batch_sync_status",
            "hp_batch_kernels_per_call", "hp_stream_open", "hp_stream_push", "hp_stream_end_beam",
-           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close")
+           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close", "hp_plan_set_allocator")
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 HP_STREAM_MAX_BEAMS = 1024
 HP_STREAM_EMPTY = 1
@@ -149,6 +152,7 @@ def lib() -> C.CDLL:
             L.hp_stream_poll.argtypes = [vp, C.POINTER(GulpResult), vp, i64, i32]
             L.hp_stream_get_stats.argtypes = [vp, C.POINTER(StreamStats)]
             L.hp_stream_close.argtypes = [vp]
+            L.hp_plan_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32

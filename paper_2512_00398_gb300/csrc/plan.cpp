@@ -32,6 +32,29 @@ int check_cuda(cudaError_t e) {
     return HP_ERR_CUDA;
 }
 
+int plan_alloc(hp_plan* p, size_t bytes, void** out) {
+    *out = nullptr;
+    if (p->alloc_fn) {
+        void* m = p->alloc_fn(bytes, p->alloc_ctx);
+        if (!m) return HP_ERR_OOM;
+        if ((uintptr_t)m & 255u) {
+            p->free_fn(m, bytes, p->alloc_ctx);
+            return HP_ERR_INVALID_ARG;
+        }
+        *out = m;
+        return HP_OK;
+    }
+    return check_cuda(cudaMalloc(out, bytes));
+}
+
+void plan_free(hp_plan* p, void* ptr, size_t bytes) {
+    if (!ptr) return;
+    if (p->free_fn)
+        p->free_fn(ptr, bytes, p->alloc_ctx);
+    else
+        cudaFree(ptr);
+}
+
 constexpr int kMaxTimedLaunches = 4096;
 
 // Record the begin event of a stage launch; returns the pair index or -1.
@@ -355,15 +378,16 @@ int ensure_device_tables(hp_plan* p) {
     const size_t o_addr = take(T.addr.size() * sizeof(uint32_t));
     const size_t o_widths = take(p->widths.size() * sizeof(int32_t));
     const size_t total = off;
-    int prev_status = 0;
+    int prev_status = p->pending_status;
+    p->pending_status = 0;
     if (p->tables) {
         if (p->status) cudaMemcpy(&prev_status, p->status, sizeof(int), cudaMemcpyDeviceToHost);
         cudaDeviceSynchronize();
-        cudaFree(p->tables);
+        plan_free(p, p->tables, p->tables_bytes);
         p->tables = nullptr;
     }
     void* mem = nullptr;
-    int rc = check_cuda(cudaMalloc(&mem, total));
+    int rc = plan_alloc(p, total, &mem);
     if (rc) return rc;
     std::vector<uint8_t> host(total, 0);
     std::memcpy(host.data() + o_status, &prev_status, sizeof(int));
@@ -374,7 +398,7 @@ int ensure_device_tables(hp_plan* p) {
     std::memcpy(host.data() + o_widths, p->widths.data(), p->widths.size() * sizeof(int32_t));
     rc = check_cuda(cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice));
     if (rc) {
-        cudaFree(mem);
+        plan_free(p, mem, total);
         return rc;
     }
     uint8_t* b = (uint8_t*)mem;
@@ -400,11 +424,11 @@ int ensure_workspace(hp_plan* p, size_t need, uint8_t** base) {
     if (p->ws_own_bytes < need) {
         if (p->ws_own) {
             cudaDeviceSynchronize();
-            cudaFree(p->ws_own);
+            plan_free(p, p->ws_own, p->ws_own_bytes);
             p->ws_own = nullptr;
             p->ws_own_bytes = 0;
         }
-        int rc = check_cuda(cudaMalloc(&p->ws_own, need));
+        int rc = plan_alloc(p, need, &p->ws_own);
         if (rc) return rc;
         p->ws_own_bytes = need;
     }
@@ -764,8 +788,8 @@ int hp_plan_destroy(hp_plan* p) {
     bool any_ev = false;
     for (int st = 0; st < HP_NUM_STAGES; ++st) any_ev = any_ev || !p->ev[st].empty();
     if (p->tables || p->ws_own || any_ev) cudaDeviceSynchronize();
-    if (p->tables) cudaFree(p->tables);
-    if (p->ws_own) cudaFree(p->ws_own);
+    plan_free(p, p->tables, p->tables_bytes);
+    plan_free(p, p->ws_own, p->ws_own_bytes);
     for (int st = 0; st < HP_NUM_STAGES; ++st)
         for (cudaEvent_t e : p->ev[st]) cudaEventDestroy(e);
     delete p;
@@ -849,6 +873,29 @@ int hp_plan_workspace_bytes(const hp_plan* p, int64_t nsamps, size_t* bytes) {
     if (!p || !bytes) return HP_ERR_INVALID_ARG;
     if (nsamps <= (int64_t)p->maxd + p->wmax) return HP_ERR_NSAMPS_TOO_SHORT;
     *bytes = make_layout(p, nsamps, true).total;
+    return HP_OK;
+}
+
+int hp_plan_set_allocator(hp_plan* p, hp_alloc_fn alloc, hp_free_fn free_fn, void* ctx) {
+    if (!p || (alloc == nullptr) != (free_fn == nullptr)) return HP_ERR_INVALID_ARG;
+    if (p->tables || p->ws_own) {
+        // return what the previous allocator gave (the tables keep the status word)
+        int st = 0;
+        if (p->status) cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaDeviceSynchronize();
+        plan_free(p, p->tables, p->tables_bytes);
+        plan_free(p, p->ws_own, p->ws_own_bytes);
+        p->tables = nullptr;
+        p->tables_bytes = 0;
+        p->tables_cfg = -1;
+        p->status = nullptr;
+        p->ws_own = nullptr;
+        p->ws_own_bytes = 0;
+        if (st != 0) p->pending_status = st;
+    }
+    p->alloc_fn = alloc;
+    p->free_fn = free_fn;
+    p->alloc_ctx = ctx;
     return HP_OK;
 }
 
@@ -1170,7 +1217,11 @@ int hp_plan_sync_status(hp_plan* p, void* stream) {
     if (!p) return HP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return HP_ERR_CUDA;
-    if (!p->status) return HP_OK;
+    if (!p->status) {
+        const int st = p->pending_status;
+        p->pending_status = 0;
+        return st;
+    }
     int st = 0;
     if (cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return HP_ERR_CUDA;

@@ -63,6 +63,12 @@ struct hp_plan {
     const uint32_t* d_addr = nullptr;
     int32_t* d_widths = nullptr;
 
+    // device allocator for the plan's tables and workspace (default cudaMalloc)
+    int pending_status = 0;        // latched status kept while the tables are reallocated
+    hp_alloc_fn alloc_fn = nullptr;
+    hp_free_fn free_fn = nullptr;
+    void* alloc_ctx = nullptr;
+
     void* ws_user = nullptr;
     size_t ws_user_bytes = 0;
     void* ws_own = nullptr;
@@ -81,6 +87,8 @@ struct hp_plan {
 namespace hp {
 
 int check_cuda(cudaError_t e);
+int plan_alloc(hp_plan* p, size_t bytes, void** out);
+void plan_free(hp_plan* p, void* ptr, size_t bytes);
 int ensure_device_tables(hp_plan* p);
 int ensure_workspace(hp_plan* p, size_t need, uint8_t** base);
 Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp);

@@ -163,3 +163,28 @@ def serve(nbeams: int = 19, gulp: int = 65536, seconds: float = 600.0, seed0: in
         pulses = _random_pulses(obs, rng, npul, dm_hi, 0.1e-3, 20e-3, 8.0, 30.0, t_hi)
         beams.append(Workload(f"beam{b}", obs, dms, synth.widths_pow2(wmax), 6.0, s, pulses))
     return beams
+
+
+def recovered(pulse, clusters, w, snr_min=10.0):
+    """Is an injected pulse found?  A cluster must lie within max(2, 5% of the
+    trials) of the nearest trial DM, start within max(W_eff, W_rep) samples of
+    the arrival at f_top minus W_rep/2, and have a width index within 1 of
+    log2(W_eff).  W_eff combines the FWHM with the smearing across the band
+    left by the nearest trial: |DM - DM_trial| times the band's delay (in
+    samples) per DM unit, from the cold-plasma law."""
+    o = w.obs
+    dms = np.asarray(w.dm_list, np.float64)
+    d_true = int(np.argmin(np.abs(dms - pulse.dm)))
+    f_lo = o.f_top + (o.nchans - 1) * o.chan_bw
+    per_dm = synth.K_DM * (f_lo ** -2 - o.f_top ** -2) / o.tsamp
+    w_eff = math.hypot(pulse.fwhm / o.tsamp, abs(dms[d_true] - pulse.dm) * per_dm)
+    tol_dm = max(2, int(round(0.05 * dms.size)))
+    for c in clusters:
+        wrep = int(w.widths[c["width_idx"]])
+        t_exp = pulse.t0 / o.tsamp - wrep / 2.0
+        if (abs(int(c["dm_idx"]) - d_true) <= tol_dm
+                and abs(int(c["sample"]) - t_exp) <= max(w_eff, wrep)
+                and abs(int(c["width_idx"]) - math.log2(max(w_eff, 1.0))) <= 1.0 + 1e-9
+                and c["snr"] >= snr_min):
+            return True
+    return False

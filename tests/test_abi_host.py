@@ -137,3 +137,21 @@ def test_stream_null_arguments():
     assert L.hp_stream_close(None) == hp.HP_OK
     h = C.c_void_p()
     assert L.hp_stream_open(C.byref(h), None, None) == hp.HP_ERR_INVALID_ARG and not h.value
+
+
+def test_plan_allocator_arguments():
+    w = workloads.tiny()
+    o = w.obs
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    L = hp.lib()
+    # an allocator needs both callables; none restores cudaMalloc
+    assert L.hp_plan_set_allocator(plan.handle, hp._lib_mod.ALLOC_FN(lambda n, c: 0),
+                                   hp._lib_mod.FREE_FN(), None) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_plan_set_allocator(None, hp._lib_mod.ALLOC_FN(), hp._lib_mod.FREE_FN(),
+                                   None) == hp.HP_ERR_INVALID_ARG
+    calls = []
+    plan.use_allocator(lambda n: calls.append(n) or 0, lambda p, n: calls.append(-n))
+    plan.use_allocator()          # nothing was allocated yet, so nothing is freed
+    assert calls == []
+    with pytest.raises(hp.HPError):
+        plan.use_allocator(lambda n: 0, None)

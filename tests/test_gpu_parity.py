@@ -358,3 +358,19 @@ def test_plan_autotune_keeps_results(hp, torch, tiny):
     cfg, ms = hp.hp_plan_autotune(p, fb)
     assert p.get_param("dedisp_config") == cfg and ms > 0
     assert np.array_equal(hp.search(p, fb), before)
+
+
+def test_torch_caching_allocator(hp, torch, tiny):
+    """Plan memory from torch's caching allocator: the same results, the
+    memory shows up in torch's accounting and is returned when the plan goes."""
+    w, s, fb = tiny
+    want = hp.search(_plan(hp, w), fb)
+    p = _plan(hp, w)
+    p.use_torch_allocator()
+    before = torch.cuda.memory_allocated()
+    got = hp.search(p, fb)
+    held = torch.cuda.memory_allocated() - before
+    assert np.array_equal(got, want)
+    assert held >= p.workspace_bytes(fb.shape[0])
+    p.close()
+    assert torch.cuda.memory_allocated() - before < held

@@ -377,29 +377,7 @@ def test_merge_permutation_invariant_and_touching_windows():
 
 # ------------------------------------------------------- whole-path pins
 
-def recovered(pulse, clusters, w, snr_min=10.0):
-    """Is an injected pulse found?  A cluster must lie within max(2, 5% of the
-    trials) of the nearest trial DM, start within max(W_eff, W_rep) samples of
-    the arrival at f_top minus W_rep/2, and have a width index within 1 of
-    log2(W_eff).  W_eff combines the FWHM with the smearing across the band
-    left by the nearest trial: |DM - DM_trial| times the band's delay (in
-    samples) per DM unit, from the cold-plasma law."""
-    o = w.obs
-    dms = np.asarray(w.dm_list, np.float64)
-    d_true = int(np.argmin(np.abs(dms - pulse.dm)))
-    f_lo = o.f_top + (o.nchans - 1) * o.chan_bw
-    per_dm = 4148.808 * (f_lo ** -2 - o.f_top ** -2) / o.tsamp
-    w_eff = math.hypot(pulse.fwhm / o.tsamp, abs(dms[d_true] - pulse.dm) * per_dm)
-    tol_dm = max(2, int(round(0.05 * dms.size)))
-    for c in clusters:
-        wrep = int(w.widths[c["width_idx"]])
-        t_exp = pulse.t0 / o.tsamp - wrep / 2.0
-        if (abs(int(c["dm_idx"]) - d_true) <= tol_dm
-                and abs(int(c["sample"]) - t_exp) <= max(w_eff, wrep)
-                and abs(int(c["width_idx"]) - math.log2(max(w_eff, 1.0))) <= 1.0 + 1e-9
-                and c["snr"] >= snr_min):
-            return True
-    return False
+from paper_2512_00398_gb300.workloads import recovered  # noqa: E402  (the recovery criterion)
 
 
 def test_injection_recovery_tiny(tiny_workload):
