@@ -104,6 +104,8 @@ def lib():
                                             C.c_int64, vp]
             L.hpo_search_window.argtypes = [vp, C.c_int64, _P(_Params), C.c_int64, C.c_int64,
                                             vp, vp, vp, C.c_int64, vp, vp, C.c_int64, vp]
+            L.hpo_rfi_clean.argtypes = [vp, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_int,
+                                        C.c_double, C.c_double, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -372,3 +374,32 @@ def stream_search(x: np.ndarray, gulp: int, f_top, chan_bw, tsamp, dm_list, widt
                                        w_tol)
         out.append({"g": g, "B0": B0, "nwin": nwin, "raw": raw, "clusters": cl})
     return out
+
+
+# ------------------------------------------------------------ c0 RFI mitigation
+@dataclass
+class RfiResult:
+    cleaned: np.ndarray       # uint8 [nsamps][nchans]
+    chan_flag: np.ndarray     # bool [nchans] narrowband channels
+    samp_flag: np.ndarray     # bool [nsamps] broadband samples
+    chan_median: np.ndarray   # int32 [nchans]
+    sigma_z: float
+
+
+def rfi_clean(x: np.ndarray, tsamp: float, nb_k: int = 5, bb_k: float = 5.0,
+              baseline_mode: int = 0, baseline_s: float = 2.0) -> RfiResult:
+    """Narrowband channel masking and zero-DM broadband excision (Sections
+    II-B and III-C; reading in hp_oracle.c)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    nsamps, nch = x.shape
+    out = np.empty_like(x)
+    cf = np.zeros(nch, np.uint8)
+    sf = np.zeros(nsamps, np.uint8)
+    med = np.zeros(nch, np.int32)
+    sg = C.c_double(0.0)
+    rc = lib().hpo_rfi_clean(_ptr(x), int(nsamps), int(nch), int(nb_k), float(bb_k),
+                             int(baseline_mode), float(baseline_s), float(tsamp), _ptr(out),
+                             _ptr(cf), _ptr(sf), _ptr(med), C.byref(sg))
+    if rc:
+        raise ValueError(f"hpo_rfi_clean rc={rc}")
+    return RfiResult(out, cf.astype(bool), sf.astype(bool), med, float(sg.value))

@@ -700,3 +700,88 @@ int hpo_search_window(const uint8_t* x, int64_t nsamps, const hpo_params* p, int
     if (tot > raw_cap) return HPO_ERR_OVERFLOW;
     return hpo_merge(raw, tot, p->widths, p->dm_tol, p->t_gap, p->w_tol, cl, cl_cap, ncl);
 }
+
+/* ------------------------------------------------------------------------
+ * Step c0: RFI mitigation before dedispersion (Section II-B "RFI
+ * Mitigation": broadband interference spans all channels, narrowband
+ * interference a few; corrupted regions are masked.  Section III-C: broadband
+ * RFI is found on the DM = 0 series, since it is not dispersed).  The paper
+ * gives no statistic or threshold; the reading used here:
+ *   - per channel c, m_c = lower median of x[.][c] and s_c = lower median of
+ *     |x[.][c] - m_c| over all samples (exact, by counting the 256 values);
+ *   - across channels, M_m = lower median of m_c, D_m = lower median of
+ *     |m_c - M_m| (likewise M_s, D_s for s_c); channel c is narrowband RFI iff
+ *     |m_c - M_m| > nb_k * max(D_m, 1) or |s_c - M_s| > nb_k * max(D_s, 1);
+ *   - z[t] = sum over channels of x[t][c], with flagged channels taking m_c;
+ *     y = z - baseline(z) (the search's baseline, step c3), sigma_z =
+ *     1.482602218505602 * median|y| (step c4); sample t is broadband RFI iff
+ *     |y[t]| >= bb_k * sigma_z (FP64; never when sigma_z = 0);
+ *   - out[t][c] = m_c where channel c or sample t is flagged, else x[t][c].
+ * ---------------------------------------------------------------------- */
+static int32_t median_of_counts(const int64_t* h, int nbins, int64_t n) {
+    /* lower median (element (n-1)/2 of the sorted values) from value counts */
+    int64_t k = (n - 1) / 2, c = 0;
+    for (int v = 0; v < nbins; ++v) {
+        c += h[v];
+        if (c > k) return v;
+    }
+    return nbins - 1;
+}
+
+int hpo_rfi_clean(const uint8_t* x, int64_t nsamps, int nchans, int nb_k, float bb_k,
+                  int baseline_mode, double baseline_s, double tsamp, uint8_t* out,
+                  uint8_t* chan_flag, uint8_t* samp_flag, int32_t* chan_median,
+                  double* sigma_z) {
+    if (nsamps < 1 || nchans < 1 || nb_k < 0 || !(bb_k > 0.0f)) return HPO_ERR_ARG;
+    int32_t* m = (int32_t*)malloc(sizeof(int32_t) * (size_t)nchans);
+    int32_t* s = (int32_t*)malloc(sizeof(int32_t) * (size_t)nchans);
+    int32_t* z = (int32_t*)malloc(sizeof(int32_t) * (size_t)nsamps);
+    int64_t* y = (int64_t*)malloc(sizeof(int64_t) * (size_t)nsamps);
+    if (!m || !s || !z || !y) { free(m); free(s); free(z); free(y); return HPO_ERR_ARG; }
+#pragma omp parallel for schedule(dynamic)
+    for (int c = 0; c < nchans; ++c) {
+        int64_t h[256] = {0}, ha[256] = {0};
+        for (int64_t t = 0; t < nsamps; ++t) h[x[t * nchans + c]]++;
+        m[c] = median_of_counts(h, 256, nsamps);
+        for (int v = 0; v < 256; ++v) ha[v > m[c] ? v - m[c] : m[c] - v] += h[v];
+        s[c] = median_of_counts(ha, 256, nsamps);
+    }
+    int64_t hm[256] = {0}, hs[256] = {0}, hdm[256] = {0}, hds[256] = {0};
+    for (int c = 0; c < nchans; ++c) { hm[m[c]]++; hs[s[c]]++; }
+    const int32_t Mm = median_of_counts(hm, 256, nchans), Ms = median_of_counts(hs, 256, nchans);
+    for (int c = 0; c < nchans; ++c) {
+        hdm[m[c] > Mm ? m[c] - Mm : Mm - m[c]]++;
+        hds[s[c] > Ms ? s[c] - Ms : Ms - s[c]]++;
+    }
+    const int64_t Dm = median_of_counts(hdm, 256, nchans), Ds = median_of_counts(hds, 256, nchans);
+    for (int c = 0; c < nchans; ++c) {
+        const int64_t dm = m[c] > Mm ? m[c] - Mm : Mm - m[c];
+        const int64_t ds = s[c] > Ms ? s[c] - Ms : Ms - s[c];
+        chan_flag[c] = dm > (int64_t)nb_k * (Dm > 1 ? Dm : 1) ||
+                       ds > (int64_t)nb_k * (Ds > 1 ? Ds : 1);
+        if (chan_median) chan_median[c] = m[c];
+    }
+#pragma omp parallel for
+    for (int64_t t = 0; t < nsamps; ++t) {
+        int64_t acc = 0;
+        for (int c = 0; c < nchans; ++c) acc += chan_flag[c] ? m[c] : x[t * nchans + c];
+        z[t] = (int32_t)acc;
+    }
+    int rc = hpo_subtract_baseline(z, nsamps, baseline_mode,
+                                   hpo_baseline_window(baseline_s, tsamp), y);
+    double sg = 0.0;
+    if (!rc) {
+        sg = hpo_sigma_from_mad(hpo_mad(y, nsamps));
+#pragma omp parallel for
+        for (int64_t t = 0; t < nsamps; ++t) {
+            const int64_t a = y[t] < 0 ? -y[t] : y[t];
+            samp_flag[t] = sg > 0.0 && (double)a >= (double)bb_k * sg;
+            for (int c = 0; c < nchans; ++c)
+                out[t * nchans + c] = (chan_flag[c] || samp_flag[t]) ? (uint8_t)m[c]
+                                                                    : x[t * nchans + c];
+        }
+    }
+    if (sigma_z) *sigma_z = sg;
+    free(m); free(s); free(z); free(y);
+    return rc ? HPO_ERR_ARG : HPO_OK;
+}

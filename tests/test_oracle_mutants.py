@@ -50,7 +50,17 @@ MUTANTS = {
                              "carry_out[k] = (double)(P[nwin + W] - P[nwin]) >= lim;"),
     "stream_no_offset": ("r.sample = best_t + t_offset;", "r.sample = best_t;"),
     "stream_peak_first_start": ("if (first == 0 && carry_in", "best_t = first;\n            if (first == 0 && carry_in"),
+    # RFI mitigation
+    "rfi_median_index": ("if (c > k) return v;", "if (c >= k) return v;"),
+    "rfi_chan_flag_inclusive": ("chan_flag[c] = dm > (int64_t)nb_k", "chan_flag[c] = dm >= (int64_t)nb_k"),
+    "rfi_zero_dm_unmasked": ("acc += chan_flag[c] ? m[c] : x[t * nchans + c];",
+                             "acc += x[t * nchans + c];"),
+    "rfi_mad_from_raw": ("ha[v > m[c] ? v - m[c] : m[c] - v] += h[v];", "ha[v] += h[v];"),
 }
+
+# the pin files that each group of mutants is checked against
+PINS = {"rfi_": ["test_oracle_rfi.py"], "stream_": ["test_oracle_stream.py"]}
+DEFAULT_PINS = ["test_oracle_pins.py", "test_oracle_stream.py"]
 
 
 @pytest.fixture(scope="module")
@@ -70,8 +80,8 @@ def test_pins_catch_mutant(name, source, tmp_path):
     subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                     "-ffp-contract=off", str(csrc), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, HPO_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    files = next((v for k, v in PINS.items() if name.startswith(k)), DEFAULT_PINS)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_stream.py")],
+                        "-k", "not stress"] + [os.path.join(ROOT, "tests", f) for f in files],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
