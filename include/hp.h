@@ -124,6 +124,9 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 22 */
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
+#define HP_PARAM_RFI 9            /* 1 = RFI mitigation before dedispersion (default 0) */
+#define HP_PARAM_RFI_NB_K 10      /* narrowband threshold, integer >= 0 (default 5) */
+#define HP_PARAM_RFI_BB_K 11      /* broadband threshold in sigma of the zero-DM series (> 0, default 5) */
 
 #define HP_NUM_DEDISP_CONFIGS 27
 
@@ -164,6 +167,27 @@ int hp_plan_bind_workspace(hp_plan* plan, void* workspace_dev, size_t bytes);
  * plan and returned by hp_plan_sync_status. */
 int hp_search(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps, void* stream,
               hp_cand_buf* cand_out);
+
+/* RFI mitigation alone (Section II-B "RFI Mitigation": broadband interference
+ * spans every channel, narrowband interference a few; Section III-C: broadband
+ * interference is found on the DM = 0 series).  The paper gives no statistic;
+ * reading: m_c = lower median of channel c, s_c = lower median of |x - m_c|;
+ * channel c is flagged iff |m_c - M_m| > nb_k max(D_m, 1) or |s_c - M_s| >
+ * nb_k max(D_s, 1), with M, D the lower median and the median absolute
+ * deviation of m_c (of s_c) across channels; z[t] = sum_c x[t][c] with flagged
+ * channels at m_c, y = z - b (the plan's baseline), sigma_z = 1.482602218505602
+ * median|y|; sample t is flagged iff |y[t]| >= bb_k sigma_z (never when
+ * sigma_z = 0); flagged channels and samples take the value m_c.  With
+ * HP_PARAM_RFI = 1, hp_search applies it before dedispersion.
+ *   filterbank_dev   device uint8 [nsamps][nchans]
+ *   cleaned_dev      optional device uint8 [nsamps][nchans] (may not alias the input)
+ *   chan_flag_dev    optional device uint8 [nchans] (1 = flagged)
+ *   samp_flag_dev    optional device uint8 [nsamps] (1 = flagged)
+ *   chan_median_dev  optional device int32 [nchans] (m_c)
+ * Uses the plan's workspace; asynchronous on `stream`. */
+int hp_rfi_clean(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps, void* stream,
+                 uint8_t* cleaned_dev, uint8_t* chan_flag_dev, uint8_t* samp_flag_dev,
+                 int32_t* chan_median_dev);
 
 /* Dedispersion alone (Section II-B, "Incoherent Dedispersion"):
  *   out_dev  device int32 [ndm][out_pitch], out_pitch >= nout, a multiple of 4;
@@ -249,7 +273,8 @@ int hp_batch_kernels_per_call(const hp_batch* batch, int64_t* kernels);
 #define HP_STAGE_DEDISP 1       /* dedispersion kernel */
 #define HP_STAGE_SEARCH 2       /* baseline, sigma, boxcars, peaks */
 #define HP_STAGE_MERGE 3        /* sort + friends-of-friends */
-#define HP_NUM_STAGES 4
+#define HP_STAGE_RFI 4          /* RFI mitigation (when HP_PARAM_RFI = 1) */
+#define HP_NUM_STAGES 5
 typedef struct {
     double stage_ms[HP_NUM_STAGES];      /* summed event time of the recorded launches */
     int64_t stage_calls[HP_NUM_STAGES];  /* launches whose events were summed */

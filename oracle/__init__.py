@@ -353,10 +353,11 @@ def gulp_geometry(g: int, gulp: int, maxd: int, wmax: int):
 
 
 def stream_search(x: np.ndarray, gulp: int, f_top, chan_bw, tsamp, dm_list, widths, thr,
-                  baseline_mode=0, baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None):
+                  baseline_mode=0, baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None, rfi=None):
     """A beam's whole series x[nsamps][nchans] searched gulp by gulp; the last
     partial gulp is dropped.  Returns one dict per gulp: g, B0, nwin, raw,
-    clusters (samples in the beam's dedispersed time)."""
+    clusters (samples in the beam's dedispersed time).  rfi=(nb_k, bb_k) cleans
+    each searched buffer first (its own statistics, step c0)."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     nch = x.shape[1]
     tab = delays(nch, f_top, chan_bw, tsamp, dm_list)
@@ -369,7 +370,10 @@ def stream_search(x: np.ndarray, gulp: int, f_top, chan_bw, tsamp, dm_list, widt
             out.append({"g": g, "B0": B0, "nwin": 0, "raw": np.empty(0, RAW_DTYPE),
                         "clusters": np.empty(0, CLUSTER_DTYPE)})
             continue
-        raw, cl, carry = search_window(x[B0:E], f_top, chan_bw, tsamp, dm_list, widths, thr,
+        buf = x[B0:E]
+        if rfi is not None:
+            buf = rfi_clean(buf, tsamp, rfi[0], rfi[1], baseline_mode, baseline_s).cleaned
+        raw, cl, carry = search_window(buf, f_top, chan_bw, tsamp, dm_list, widths, thr,
                                        nwin, B0, carry, baseline_mode, baseline_s, dm_tol, t_gap,
                                        w_tol)
         out.append({"g": g, "B0": B0, "nwin": nwin, "raw": raw, "clusters": cl})

@@ -18,6 +18,7 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_NUM_STAGES, HP_OK, HP_PARAM_BASELINE_MODE, HP_PARAM_BASELINE_S,
                    HP_PARAM_DEDISP_CONFIG, HP_PARAM_DM_TOL, HP_PARAM_RAW_CAPACITY,
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
+                   HP_PARAM_RFI, HP_PARAM_RFI_NB_K, HP_PARAM_RFI_BB_K, HP_STAGE_RFI,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
                    STAGE_NAMES, HP_BATCH_MAX_FILES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks,
                    Stats, HP_STREAM_EMPTY, HP_STREAM_MAX_BEAMS, check, lib, status_str)
@@ -26,7 +27,8 @@ from . import _lib as _lib_mod
 _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASELINE_S,
            "dm_tol": HP_PARAM_DM_TOL, "t_gap": HP_PARAM_T_GAP, "w_tol": HP_PARAM_W_TOL,
            "raw_capacity": HP_PARAM_RAW_CAPACITY, "dedisp_config": HP_PARAM_DEDISP_CONFIG,
-           "stage_timing": HP_PARAM_STAGE_TIMING, "timeout_s": HP_PARAM_TIMEOUT_S}
+           "stage_timing": HP_PARAM_STAGE_TIMING, "timeout_s": HP_PARAM_TIMEOUT_S,
+           "rfi": HP_PARAM_RFI, "rfi_nb_k": HP_PARAM_RFI_NB_K, "rfi_bb_k": HP_PARAM_RFI_BB_K}
 
 
 def _torch():
@@ -267,6 +269,24 @@ def hp_merge_static(raw, raw_count, sigma, widths, dm_tol=1, t_gap=0, w_tol=None
                                 int(w.size if w_tol is None else w_tol), _stream_ptr(stream),
                                 C.byref(b)), "hp_merge_static")
     return data, count
+
+
+def hp_rfi_clean(plan: Plan, filterbank, stream=None, cleaned: bool = True):
+    """RFI mitigation alone: returns (cleaned uint8 [nsamps][nchans] or None,
+    channel flags, sample flags, channel medians) as device tensors."""
+    import torch
+    _check_fb(plan, filterbank)
+    n = int(filterbank.shape[0])
+    dev = filterbank.device
+    out = torch.empty_like(filterbank) if cleaned else None
+    cf = torch.empty(plan.nchans, dtype=torch.uint8, device=dev)
+    sf = torch.empty(n, dtype=torch.uint8, device=dev)
+    med = torch.empty(plan.nchans, dtype=torch.int32, device=dev)
+    check(lib().hp_rfi_clean(plan.handle, C.c_void_p(filterbank.data_ptr()), n, _stream_ptr(stream),
+                             C.c_void_p(out.data_ptr()) if out is not None else None,
+                             C.c_void_p(cf.data_ptr()), C.c_void_p(sf.data_ptr()),
+                             C.c_void_p(med.data_ptr())), "hp_rfi_clean")
+    return out, cf, sf, med
 
 
 def hp_plan_autotune(plan: Plan, filterbank, stream=None):

@@ -31,11 +31,14 @@ HP_PARAM_RAW_CAPACITY = 5
 HP_PARAM_DEDISP_CONFIG = 6
 HP_PARAM_STAGE_TIMING = 7
 HP_PARAM_TIMEOUT_S = 8
+HP_PARAM_RFI = 9
+HP_PARAM_RFI_NB_K = 10
+HP_PARAM_RFI_BB_K = 11
 HP_NUM_DEDISP_CONFIGS = 27
 
-HP_STAGE_TRANSPOSE, HP_STAGE_DEDISP, HP_STAGE_SEARCH, HP_STAGE_MERGE = 0, 1, 2, 3
-HP_NUM_STAGES = 4
-STAGE_NAMES = ("transpose", "dedisp", "search", "merge")
+HP_STAGE_TRANSPOSE, HP_STAGE_DEDISP, HP_STAGE_SEARCH, HP_STAGE_MERGE, HP_STAGE_RFI = 0, 1, 2, 3, 4
+HP_NUM_STAGES = 5
+STAGE_NAMES = ("transpose", "dedisp", "search", "merge", "rfi")
 
 #: hp_cand (48 bytes)
 CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("width_idx", "<i4"), ("sample", "<i8"),
@@ -53,7 +56,7 @@ EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_pa
            "hp_plan_autotune", "hp_batch_create", "hp_batch_destroy", "hp_batch_set_config",
            "hp_batch_autotune", "hp_batch_search", "hp_batch_sync_status",
            "hp_batch_kernels_per_call", "hp_stream_open", "hp_stream_push", "hp_stream_end_beam",
-           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close", "hp_plan_set_allocator")
+           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close", "hp_plan_set_allocator", "hp_rfi_clean")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -153,6 +156,7 @@ def lib() -> C.CDLL:
             L.hp_stream_get_stats.argtypes = [vp, C.POINTER(StreamStats)]
             L.hp_stream_close.argtypes = [vp]
             L.hp_plan_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
+            L.hp_rfi_clean.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32

@@ -192,8 +192,32 @@ struct SearchArgs {
     const uint8_t* carry_in;
     uint8_t* carry_out;
     int64_t t_offset;
+    // 1: stop after sigma and the integer thresholds (no detection); used for the
+    // zero-DM series of the RFI stage
+    int stats_only;
 };
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch);
+
+// RFI mitigation of one filterbank before dedispersion (rfi.cu).  Works on the
+// transposed copy xt [nch][xt_pitch] (cleaned in place); the time-major input
+// x [nsamps][nch] is read only for the optional cleaned copy `out`.
+struct RfiArgs {
+    const uint8_t* x;          // [nsamps][nch]
+    uint8_t* xt;               // [nch][xt_pitch], NULL: leave it alone
+    int64_t xt_pitch;
+    int64_t nsamps;
+    int nch;
+    int nb_k;                  // narrowband threshold (channel-statistics MADs)
+    uint32_t* hist;            // scratch [nch][256]
+    int32_t* med;              // [nch] channel medians m_c
+    int32_t* spread;           // [nch] channel median |x - m_c|
+    uint8_t* chan_flag;        // [round16(nch)] 1 = narrowband channel
+    uint8_t* samp_flag;        // [round16(nsamps) + 16] 1 = broadband sample
+    int32_t* one;              // device int32 holding 1 (the width list of the z search)
+    SearchArgs z;              // statistics of the zero-DM series z (stats_only)
+    uint8_t* out;              // optional [nsamps][nch] cleaned copy of x
+};
+cudaError_t launch_rfi(const RfiArgs& r, cudaStream_t s, int64_t* nlaunch);
 
 struct MergeArgs {
     const hp_raw_cand* raw;

@@ -300,6 +300,38 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
         L.xt = take((size_t)p->nchans * L.xt_pitch);
         L.D = take((size_t)ndm * L.dpitch * 4);
     }
+    // RFI stage (small: per-channel counts and one int32 series of nsamps)
+    {
+        const int nch = p->nchans;
+        const int64_t n = std::max<int64_t>(nsamps, 1);
+        L.r_hist = take((size_t)nch * 256 * 4);
+        L.r_med = take((size_t)nch * 4);
+        L.r_spread = take((size_t)nch * 4);
+        L.r_cflag = take(align_up((size_t)nch, 16));
+        L.r_sflag = take((size_t)round_up64(n, 16) + 16);
+        L.r_one = take(16);
+        L.r_zpitch = round_up64(n, 64);
+        L.r_z = take((size_t)L.r_zpitch * 4);
+        const int lv = remedian_levels(baseline_window(p));
+        const int q1 = std::min(lv, 5), q2 = std::min(std::max(lv - 5, 0), 5);
+        int64_t p1 = 1, p2 = 1;
+        for (int i = 0; i < q1; ++i) p1 *= 5;
+        for (int i = 0; i < q2; ++i) p2 *= 5;
+        const int64_t n1 = ceil_div(n, p1);
+        L.r_lvl_pitch_a = round_up64(std::max<int64_t>(n1, 1), 4);
+        L.r_lvl_pitch_b = round_up64(std::max<int64_t>(ceil_div(n1, p2), 1), 4);
+        L.r_lvl_a = take((size_t)L.r_lvl_pitch_a * 4);
+        L.r_lvl_b = take((size_t)L.r_lvl_pitch_b * 4);
+        L.r_mean_pitch = ceil_div(n, 32) + 1;
+        L.r_mean = take(p->baseline_mode == 1 ? (size_t)L.r_mean_pitch * 8 : 0);
+        L.r_zhist = take((size_t)kHistBins * 4);
+        L.r_bucket = take(8);
+        L.r_rank = take(8);
+        L.r_mad = take(8);
+        L.r_sigma = take(8);
+        L.r_tint = take(8);
+        L.r_y = take(p->baseline_mode == 1 ? (size_t)L.r_zpitch * 4 : 0);
+    }
     L.search_begin = off;
     // y = D - b: written over the plan's own dedispersed series in median mode
     // (whose baseline reads only the remedian knots); a separate array in mean
@@ -454,13 +486,21 @@ DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_
 }
 
 int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, uint8_t* xt, int64_t xt_pitch,
-               int32_t* out, int64_t out_pitch, cudaStream_t s) {
+               int32_t* out, int64_t out_pitch, cudaStream_t s, const Layout* rfi_L = nullptr,
+               uint8_t* rfi_ws = nullptr) {
     const int64_t nout = nsamps - p->maxd;
     int ti = stage_begin(p, HP_STAGE_TRANSPOSE, s);
     int rc = check_cuda(launch_transpose(fb, nsamps, p->nchans, xt, xt_pitch, s));
     stage_end(p, HP_STAGE_TRANSPOSE, ti, s);
     if (rc) return rc;
     ++p->launches;
+    if (p->rfi && rfi_ws) {
+        const RfiArgs r = make_rfi_args(p, *rfi_L, rfi_ws, fb, xt, xt_pitch, nsamps, nullptr);
+        ti = stage_begin(p, HP_STAGE_RFI, s);
+        rc = check_cuda(launch_rfi(r, s, &p->launches));
+        stage_end(p, HP_STAGE_RFI, ti, s);
+        if (rc) return rc;
+    }
     DedispBatch B;   // copied into the kernel parameters at launch
     std::memset(&B, 0, sizeof(B));
     B.njobs = 1;
@@ -526,7 +566,59 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.carry_in = nullptr;
     a.carry_out = nullptr;
     a.t_offset = 0;
+    a.stats_only = 0;
     return a;
+}
+
+RfiArgs make_rfi_args(hp_plan* p, const Layout& L, uint8_t* ws, const uint8_t* x, uint8_t* xt,
+                      int64_t xt_pitch, int64_t nsamps, uint8_t* out) {
+    RfiArgs r;
+    r.x = x;
+    r.xt = xt;
+    r.xt_pitch = xt_pitch;
+    r.nsamps = nsamps;
+    r.nch = p->nchans;
+    r.nb_k = p->rfi_nb_k;
+    r.hist = (uint32_t*)(ws + L.r_hist);
+    r.med = (int32_t*)(ws + L.r_med);
+    r.spread = (int32_t*)(ws + L.r_spread);
+    r.chan_flag = ws + L.r_cflag;
+    r.samp_flag = ws + L.r_sflag;
+    r.one = (int32_t*)(ws + L.r_one);
+    r.out = out;
+    // the zero-DM series as a one-trial, one-width (W = 1) stats-only search
+    SearchArgs& z = r.z;
+    std::memset(&z, 0, sizeof(z));
+    int32_t* zs = (int32_t*)(ws + L.r_z);
+    z.D = zs;
+    z.pitch = L.r_zpitch;
+    z.nout = nsamps;
+    z.ndm = 1;
+    z.nw = 1;
+    z.widths = r.one;
+    z.wmax = 1;
+    z.thr = p->rfi_bb_k;
+    z.baseline_mode = p->baseline_mode;
+    z.win = baseline_window(p);
+    z.levels = remedian_levels(z.win);
+    z.lvl_a = (int32_t*)(ws + L.r_lvl_a);
+    z.lvl_b = (int32_t*)(ws + L.r_lvl_b);
+    z.lvl_pitch_a = L.r_lvl_pitch_a;
+    z.lvl_pitch_b = L.r_lvl_pitch_b;
+    z.mean_pre = (int64_t*)(ws + L.r_mean);
+    z.mean_pitch = L.r_mean_pitch;
+    z.hist = (uint32_t*)(ws + L.r_zhist);
+    z.refine_bucket = (int32_t*)(ws + L.r_bucket);
+    z.refine_rank = (int64_t*)(ws + L.r_rank);
+    z.mad = (int64_t*)(ws + L.r_mad);
+    z.sigma = (double*)(ws + L.r_sigma);
+    z.tint = (int64_t*)(ws + L.r_tint);
+    z.status = p->status;
+    z.Y = p->baseline_mode == 1 ? (int32_t*)(ws + L.r_y) : zs;   // in place in median mode
+    z.ypitch = L.r_zpitch;
+    z.nwin = nsamps;
+    z.stats_only = 1;
+    return r;
 }
 
 MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw_cand* raw,
@@ -666,6 +758,15 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
     int rc = check_cuda(launch_transpose_batch(tb, s));
     if (rc) return rc;
     ++k;
+    for (int i = 0; i < n; ++i) {          // RFI mitigation of the files that ask for it
+        hp_plan* p = b->plans[i];
+        if (!p->rfi) continue;
+        const Layout& L = Ls[i];
+        const RfiArgs r = make_rfi_args(p, L, wss[i], fbs[i], wss[i] + L.xt, L.xt_pitch,
+                                        nsamps[i], nullptr);
+        rc = check_cuda(launch_rfi(r, s, &k));
+        if (rc) return rc;
+    }
     hp_plan* p0 = b->plans[0];
     rc = check_cuda(launch_dedisp(b->cfg, db, p0->status, p0->timeout_ns, s));
     if (rc) return rc;
@@ -719,6 +820,9 @@ std::vector<uintptr_t> batch_key(const hp_batch* b, const uint8_t* const* fbs,
         k.push_back((uintptr_t)p->w_tol);
         k.push_back((uintptr_t)p->raw_capacity);
         k.push_back((uintptr_t)p->timeout_ns);
+        k.push_back((uintptr_t)p->rfi);
+        k.push_back((uintptr_t)p->rfi_nb_k);
+        k.push_back((uintptr_t)(p->rfi_bb_k * 1e6));
     }
     return k;
 }
@@ -836,6 +940,18 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
             if (!(v > 0.0) || v > 3600.0) return HP_ERR_INVALID_ARG;
             p->timeout_ns = (uint64_t)(v * 1e9);
             return HP_OK;
+        case HP_PARAM_RFI:
+            if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
+            p->rfi = v != 0.0;
+            return HP_OK;
+        case HP_PARAM_RFI_NB_K:
+            if (v < 0 || v > 255 || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->rfi_nb_k = (int)v;
+            return HP_OK;
+        case HP_PARAM_RFI_BB_K:
+            if (!(v > 0.0) || v > 1e6) return HP_ERR_INVALID_ARG;
+            p->rfi_bb_k = (float)v;
+            return HP_OK;
         default:
             return HP_ERR_INVALID_ARG;
     }
@@ -853,6 +969,9 @@ int hp_plan_get_param(const hp_plan* p, int param, double* v) {
         case HP_PARAM_DEDISP_CONFIG: *v = p->dedisp_cfg; return HP_OK;
         case HP_PARAM_STAGE_TIMING: *v = p->timing ? 1.0 : 0.0; return HP_OK;
         case HP_PARAM_TIMEOUT_S: *v = (double)p->timeout_ns * 1e-9; return HP_OK;
+        case HP_PARAM_RFI: *v = p->rfi ? 1.0 : 0.0; return HP_OK;
+        case HP_PARAM_RFI_NB_K: *v = p->rfi_nb_k; return HP_OK;
+        case HP_PARAM_RFI_BB_K: *v = (double)p->rfi_bb_k; return HP_OK;
         default: return HP_ERR_INVALID_ARG;
     }
 }
@@ -907,6 +1026,35 @@ int hp_plan_bind_workspace(hp_plan* p, void* ws, size_t bytes) {
     return HP_OK;
 }
 
+int hp_rfi_clean(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream, uint8_t* cleaned,
+                 uint8_t* chan_flag, uint8_t* samp_flag, int32_t* chan_median) {
+    if (!p || !fb || nsamps < 1 || nsamps >= kMaxSamples) return HP_ERR_INVALID_ARG;
+    if (cleaned == fb) return HP_ERR_INVALID_ARG;
+    int rc = ensure_device_tables(p);
+    if (rc) return rc;
+    Layout L = make_layout(p, std::max<int64_t>(nsamps, (int64_t)p->maxd + 1), true);
+    uint8_t* ws = nullptr;
+    rc = ensure_workspace(p, L.total, &ws);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = check_cuda(launch_transpose(fb, nsamps, p->nchans, ws + L.xt, L.xt_pitch, s));
+    if (rc) return rc;
+    ++p->launches;
+    const RfiArgs r = make_rfi_args(p, L, ws, fb, ws + L.xt, L.xt_pitch, nsamps, cleaned);
+    rc = check_cuda(launch_rfi(r, s, &p->launches));
+    if (rc) return rc;
+    if (chan_flag)
+        rc = check_cuda(cudaMemcpyAsync(chan_flag, r.chan_flag, (size_t)p->nchans,
+                                        cudaMemcpyDeviceToDevice, s));
+    if (!rc && samp_flag)
+        rc = check_cuda(cudaMemcpyAsync(samp_flag, r.samp_flag, (size_t)nsamps,
+                                        cudaMemcpyDeviceToDevice, s));
+    if (!rc && chan_median)
+        rc = check_cuda(cudaMemcpyAsync(chan_median, r.med, (size_t)p->nchans * 4,
+                                        cudaMemcpyDeviceToDevice, s));
+    return rc;
+}
+
 int hp_dedisperse(hp_plan* p, const uint8_t* fb, int64_t nsamps, int32_t* out, int64_t pitch,
                   void* stream) {
     int rc = validate_search_input(p, fb, nsamps);
@@ -919,7 +1067,8 @@ int hp_dedisperse(hp_plan* p, const uint8_t* fb, int64_t nsamps, int32_t* out, i
     uint8_t* ws = nullptr;
     rc = ensure_workspace(p, L.total, &ws);
     if (rc) return rc;
-    return run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, out, pitch, (cudaStream_t)stream);
+    return run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, out, pitch, (cudaStream_t)stream, &L,
+                      ws);
 }
 
 int hp_detect(hp_plan* p, const int32_t* series, int64_t nout, int64_t pitch, void* stream,
@@ -982,7 +1131,7 @@ int hp_search(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream, hp_ca
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t* D = (int32_t*)(ws + L.D);
-    rc = run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, D, L.dpitch, s);
+    rc = run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, D, L.dpitch, s, &L, ws);
     if (rc) return rc;
     hp_raw_cand* raw = (hp_raw_cand*)(ws + L.raw);
     int64_t* raw_count = (int64_t*)(ws + L.raw_count);

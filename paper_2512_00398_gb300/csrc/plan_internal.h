@@ -22,6 +22,12 @@ struct Layout {
            mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
            vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
            dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
+    // RFI stage: channel counts, statistics and flags, the zero-DM series and
+    // the scratch of its statistics (a one-trial stats-only search)
+    size_t r_hist = 0, r_med = 0, r_spread = 0, r_cflag = 0, r_sflag = 0, r_one = 0, r_z = 0,
+           r_lvl_a = 0, r_lvl_b = 0, r_mean = 0, r_zhist = 0, r_bucket = 0, r_rank = 0,
+           r_mad = 0, r_sigma = 0, r_tint = 0, r_y = 0;
+    int64_t r_zpitch = 0, r_lvl_pitch_a = 0, r_lvl_pitch_b = 0, r_mean_pitch = 0;
     size_t y = 0;              // baseline-subtracted series (unless it overwrites D)
     int64_t ypitch = 0;
     bool y_in_D = false;
@@ -64,6 +70,9 @@ struct hp_plan {
     int32_t* d_widths = nullptr;
 
     // device allocator for the plan's tables and workspace (default cudaMalloc)
+    bool rfi = false;              // RFI mitigation before dedispersion
+    int rfi_nb_k = 5;
+    float rfi_bb_k = 5.0f;
     int pending_status = 0;        // latched status kept while the tables are reallocated
     hp_alloc_fn alloc_fn = nullptr;
     hp_free_fn free_fn = nullptr;
@@ -77,7 +86,7 @@ struct hp_plan {
     // stage timing (events on the launching stream) and launch accounting
     bool timing = false;
     std::vector<cudaEvent_t> ev[HP_NUM_STAGES];   // pairs (begin, end)
-    int ev_used[HP_NUM_STAGES] = {0, 0, 0, 0};
+    int ev_used[HP_NUM_STAGES] = {};
     int64_t launches = 0;
 
     int ndm() const { return (int)dm_list.size(); }
@@ -99,6 +108,8 @@ DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_
 SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int32_t* D,
                             int64_t pitch, int64_t nout, hp_raw_cand* raw, int64_t raw_cap,
                             int64_t* raw_count);
+RfiArgs make_rfi_args(hp_plan* p, const Layout& L, uint8_t* ws, const uint8_t* x, uint8_t* xt,
+                      int64_t xt_pitch, int64_t nsamps, uint8_t* out);
 MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw_cand* raw,
                           const int64_t* nraw, int64_t raw_cap, const double* sigma,
                           hp_cand_buf* out);

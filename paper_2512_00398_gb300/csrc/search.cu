@@ -702,6 +702,7 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
     sigma_kernel<<<(unsigned)ceil_div(ndm, 128), 128, 0, s>>>(a.mad, ndm, a.widths, a.nw, a.thr,
                                                               a.sigma, a.tint);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.stats_only) return cudaSuccess;
     const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
     if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
@@ -722,8 +723,10 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
     const int64_t n = a.nout;
     const int ndm = a.ndm;
     if (ndm <= 0 || n <= 0) return cudaSuccess;
-    if ((e = cudaMemsetAsync(a.raw_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.tail_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+    if (!a.stats_only) {
+        if ((e = cudaMemsetAsync(a.raw_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(a.tail_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+    }
     if ((e = cudaMemsetAsync(a.hist, 0, (size_t)ndm * kHistBins * 4, s)) != cudaSuccess) return e;
 
     BaselineCtx bc{};

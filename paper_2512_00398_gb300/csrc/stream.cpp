@@ -298,6 +298,12 @@ int enqueue_step(hp_stream* s, Step* st) {
     if (n > 0) {
         tb.njobs = db.njobs = n;
         rc = check_cuda(launch_transpose_batch(tb, m));
+        int64_t rfi_kernels = 0;
+        for (int j = 0; j < n && !rc && p->rfi; ++j) {   // RFI mitigation per searched buffer
+            const RfiArgs r = make_rfi_args(p, Ls[j], s->ws[j], nullptr, s->ws[j] + Ls[j].xt,
+                                            Ls[j].xt_pitch, work[j]->E - work[j]->B0, nullptr);
+            rc = check_cuda(launch_rfi(r, m, &rfi_kernels));
+        }
         if (!rc) rc = check_cuda(launch_dedisp(p->dedisp_cfg, db, p->status, p->timeout_ns, m));
         if (!rc) rc = check_cuda(cudaEventRecord(s->fork, m));
         if (rc) return rc;
@@ -392,6 +398,9 @@ int copy_plan(const hp_plan* t, int64_t raw_capacity, hp_plan** out) {
     p->dedisp_cfg = t->dedisp_cfg;
     p->timeout_ns = t->timeout_ns;
     p->raw_capacity = raw_capacity;
+    p->rfi = t->rfi;
+    p->rfi_nb_k = t->rfi_nb_k;
+    p->rfi_bb_k = t->rfi_bb_k;
     return HP_OK;
 }
 

@@ -155,3 +155,19 @@ def test_plan_allocator_arguments():
     assert calls == []
     with pytest.raises(hp.HPError):
         plan.use_allocator(lambda n: 0, None)
+
+
+def test_rfi_params():
+    w = workloads.tiny()
+    o = w.obs
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    assert plan.get_param("rfi") == 0 and plan.get_param("rfi_nb_k") == 5
+    assert plan.get_param("rfi_bb_k") == 5.0
+    plan.set_param("rfi", 1)
+    plan.set_param("rfi_nb_k", 3)
+    plan.set_param("rfi_bb_k", 4.5)
+    assert (plan.get_param("rfi"), plan.get_param("rfi_nb_k"), plan.get_param("rfi_bb_k")) == \
+        (1, 3, 4.5)
+    for name, bad in (("rfi", 2), ("rfi_nb_k", -1), ("rfi_nb_k", 2.5), ("rfi_bb_k", 0.0)):
+        with pytest.raises(hp.HPError):
+            plan.set_param(name, bad)

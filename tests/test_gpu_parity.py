@@ -374,3 +374,20 @@ def test_torch_caching_allocator(hp, torch, tiny):
     assert held >= p.workspace_bytes(fb.shape[0])
     p.close()
     assert torch.cuda.memory_allocated() - before < held
+
+
+def test_batch_with_rfi_matches_per_file(hp, torch):
+    files = _small_batch(nfiles=3)
+    fbs = []
+    for w in files:
+        x = w.generate().data.astype(np.int32)
+        x[:, [1, 2]] += 50
+        x[::5000, :] += 60
+        fbs.append(torch.from_numpy(np.clip(x, 0, 255).astype(np.uint8)).cuda())
+    plans = [_plan(hp, w, rfi=1) for w in files]
+    want = [hp.search(p, fb) for p, fb in zip(plans, fbs)]
+    b = hp.Batch(plans)
+    for _ in range(2):
+        for g, w_ in zip(b.search(fbs), want):
+            assert np.array_equal(g, w_)
+    b.close()

@@ -145,3 +145,22 @@ def test_stream_argument_errors(env, beams):
     st.close()
     with pytest.raises(hp.HPError):
         hp.Stream(plan, nbeams=2, gulp=G, hbm_budget=1 << 20)   # cannot hold one slot
+
+
+def test_stream_with_rfi_matches_oracle(env, beams):
+    """Each searched buffer cleaned on its own before the search (HP_PARAM_RFI)."""
+    torch, hp = env
+    ws, data, want = beams
+    w = ws[0]
+    o = w.obs
+    x = data[0].astype(np.int32)
+    x[:, [7, 90]] += 50
+    x[::3001, :] += 60
+    x = np.clip(x, 0, 255).astype(np.uint8)
+    plan = _plan(hp, w)
+    plan.set_param("rfi", 1)
+    got, _, _ = _run(hp, plan, [x], [(0, g) for g in range(8)])
+    ref = oracle.stream_search(x, G, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths,
+                               w.threshold, rfi=(5, 5.0))
+    for r in ref:
+        _same(got[(0, r["g"])][1], r["clusters"])
