@@ -391,3 +391,34 @@ def test_batch_with_rfi_matches_per_file(hp, torch):
         for g, w_ in zip(b.search(fbs), want):
             assert np.array_equal(g, w_)
     b.close()
+
+
+@pytest.mark.parametrize("case", ["one_channel", "one_trial_one_width", "widest_boxcar"])
+def test_degenerate_and_maximum_shapes(hp, torch, case):
+    """One channel (every delay 0), a single trial and width, and the widest
+    boxcar the library accepts (16384 samples, a detect halo four tiles long),
+    each compared exactly with the oracle."""
+    rng = np.random.default_rng({"one_channel": 1, "one_trial_one_width": 2,
+                                 "widest_boxcar": 3}[case])
+    if case == "one_channel":
+        nch, nsamps, dms, widths = 1, 30000, np.array([0.0, 50.0], np.float32), [1, 2, 4, 8]
+    elif case == "one_trial_one_width":
+        nch, nsamps, dms, widths = 48, 20000, np.array([12.0], np.float32), [3]
+    else:
+        nch, nsamps, dms = 32, 120000, np.array([0.0, 20.0, 40.0], np.float32)
+        widths = [1, 64, 4096, 16384]
+    x = rng.normal(100, 10, size=(nsamps, nch))
+    x[nsamps // 3: nsamps // 3 + 9] += 40
+    x[nsamps // 2: nsamps // 2 + 20000] += 1.5      # a long weak plateau for the wide boxcars
+    x = np.clip(np.rint(x), 0, 255).astype(np.uint8)
+    widths = np.array(widths, np.int32)
+    want = oracle.search(x, 1500.0, -2.0, 1e-3, dms, widths, 5.0)
+    p = hp.Plan(nch, 1500.0, -2.0, 1e-3, dms, widths, 5.0)
+    fb = torch.from_numpy(x).cuda()
+    D = hp.hp_dedisperse(p, fb)
+    tab = p.delays()
+    assert np.array_equal(D[:, :p.nout(nsamps)].cpu().numpy(), oracle.dedisperse(x, tab))
+    raw_g, sig_g, _ = hp.detect(p, D, p.nout(nsamps))
+    assert np.array_equal(sig_g, want.sigma)
+    assert _key(raw_g) == _key(want.raw) and len(want.raw) > 0
+    _compare_clusters(hp.search(p, fb), want.clusters, 5.0)
