@@ -188,7 +188,7 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                 rows += g.smem;
                 ++n;
             }
-            StageDesc sd;
+            StageDesc sd{};
             sd.chan_begin = (uint32_t)T->chans.size();
             sd.nchan = (uint32_t)n;
             sd.addr_off = (uint32_t)align_up((size_t)n * sizeof(ChanDesc), 16);
@@ -468,6 +468,13 @@ int ensure_workspace(hp_plan* p, size_t need, uint8_t** base) {
     return HP_OK;
 }
 
+// Every staged row of the last time tile stays inside the transposed row (the
+// copies never read past the buffer).
+bool reach_ok(const hp_plan* p, int64_t nout, int64_t xt_pitch) {
+    const int64_t last_t0 = (ceil_div(nout, p->tiling.BT) - 1) * (int64_t)p->tiling.BT;
+    return last_t0 + p->tiling.max_reach <= xt_pitch;
+}
+
 DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_t* out,
                    int64_t out_pitch, int64_t nout) {
     DedispJob J;
@@ -478,6 +485,7 @@ DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_
     J.nout = nout;
     J.ntt = (int32_t)ceil_div(nout, p->tiling.BT);
     J.ndt = (int32_t)p->tiling.tiles.size();
+    if (!reach_ok(p, nout, xt_pitch)) J.ntt = J.ndt = 0;   // callers report the error
     J.tiles = p->d_tiles;
     J.stages = p->d_stages;
     J.chans = p->d_chans;
@@ -504,6 +512,7 @@ int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, uint8_t* xt, int64
     DedispBatch B;   // copied into the kernel parameters at launch
     std::memset(&B, 0, sizeof(B));
     B.njobs = 1;
+    if (!reach_ok(p, nout, xt_pitch)) return HP_ERR_INVALID_ARG;
     B.jobs[0] = make_job(p, xt, xt_pitch, out, out_pitch, nout);
     B.prefix[0] = 0;
     B.prefix[1] = (int64_t)B.jobs[0].ntt * B.jobs[0].ndt;
@@ -750,6 +759,7 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         const Layout& L = Ls[i];
         tb.jobs[i] = make_transpose_job(fbs[i], nsamps[i], p->nchans, wss[i] + L.xt, L.xt_pitch);
         tb.prefix[i + 1] = tb.prefix[i] + tb.jobs[i].ttiles * tb.jobs[i].ctiles;
+        if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
         db.jobs[i] = make_job(p, wss[i] + L.xt, L.xt_pitch, (int32_t*)(wss[i] + L.D), L.dpitch,
                               L.nout);
         db.prefix[i + 1] = db.prefix[i] + (int64_t)db.jobs[i].ntt * db.jobs[i].ndt;
@@ -1306,15 +1316,18 @@ int hp_batch_autotune(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsa
         DedispBatch db;
         std::memset(&db, 0, sizeof(db));
         tb.njobs = db.njobs = n;
+        bool reach = true;
         for (int i = 0; i < n; ++i) {
             hp_plan* p = b->plans[i];
             const Layout& L = Ls[i];
+            reach = reach && reach_ok(p, L.nout, L.xt_pitch);
             tb.jobs[i] = make_transpose_job(fbs[i], nsamps[i], p->nchans, wss[i] + L.xt, L.xt_pitch);
             tb.prefix[i + 1] = tb.prefix[i] + tb.jobs[i].ttiles * tb.jobs[i].ctiles;
             db.jobs[i] = make_job(p, wss[i] + L.xt, L.xt_pitch, (int32_t*)(wss[i] + L.D), L.dpitch,
                                   L.nout);
             db.prefix[i + 1] = db.prefix[i] + (int64_t)db.jobs[i].ntt * db.jobs[i].ndt;
         }
+        if (!reach) continue;          // this tile shape cannot stage these rows
         hp_plan* p0 = b->plans[0];
         if (!warm) {   // one untimed pass before the first timed one
             rc = check_cuda(launch_transpose_batch(tb, s));

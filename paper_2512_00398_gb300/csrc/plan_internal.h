@@ -103,6 +103,7 @@ int ensure_workspace(hp_plan* p, size_t need, uint8_t** base);
 Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp);
 int64_t xt_pitch_for(int64_t nsamps);
 int validate_search_input(const hp_plan* p, const void* ptr, int64_t nsamps);
+bool reach_ok(const hp_plan* p, int64_t nout, int64_t xt_pitch);
 DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_t* out,
                    int64_t out_pitch, int64_t nout);
 SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int32_t* D,

@@ -290,6 +290,7 @@ int enqueue_step(hp_stream* s, Step* st) {
         J.ring_slots = s->R;
         tb.jobs[j] = J;
         tb.prefix[j + 1] = tb.prefix[j] + J.ttiles * J.ctiles;
+        if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
         db.jobs[j] = make_job(p, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, L.nout);
         db.prefix[j + 1] = db.prefix[j] + (int64_t)db.jobs[j].ntt * db.jobs[j].ndt;
         work.push_back(&it);
