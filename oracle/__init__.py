@@ -58,7 +58,8 @@ class _Params(C.Structure):
                 ("tsamp", C.c_double), ("dm_list", _P(C.c_float)), ("ndm", C.c_int),
                 ("widths", _P(C.c_int32)), ("nw", C.c_int), ("thr", C.c_float),
                 ("baseline_mode", C.c_int), ("baseline_s", C.c_double), ("dm_tol", C.c_int),
-                ("t_gap", C.c_int64), ("w_tol", C.c_int)]
+                ("t_gap", C.c_int64), ("w_tol", C.c_int), ("subband_chans", C.c_int),
+                ("subband_group", C.c_int)]
 
 
 def lib():
@@ -76,6 +77,7 @@ def lib():
             L.hpo_max_delay.restype = C.c_int32
             L.hpo_dedisperse_rows.argtypes = [vp, C.c_int64, C.c_int, vp, C.c_int, C.c_int,
                                               C.c_int64, vp]
+            L.hpo_subband_delays.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
             L.hpo_dedisperse_point.argtypes = [vp, C.c_int, vp, C.c_int64]
             L.hpo_dedisperse_point.restype = C.c_int64
             L.hpo_remedian_levels.argtypes = [C.c_int64]
@@ -127,6 +129,20 @@ def delays(nchans, f_top, chan_bw, tsamp, dm_list) -> np.ndarray:
                           int(dm.size), _ptr(out))
     if rc:
         raise ValueError(f"hpo_delays rc={rc}")
+    return out
+
+
+def subband_delays(delay_table: np.ndarray, S: int, G: int) -> np.ndarray:
+    """Effective table of two-stage (sub-band) dedispersion: sub-bands of S
+    channels, groups of G trials with nominal trial g*G + (len-1)//2;
+    e[d][c] = delay[d][top] + delay[n][c] - delay[n][top] (top = c//S*S,
+    n = the nominal trial of d's group).  A variant of step c2."""
+    dt = np.ascontiguousarray(delay_table, dtype=np.int32)
+    ndm, nch = dt.shape
+    out = np.empty_like(dt)
+    rc = lib().hpo_subband_delays(_ptr(dt), int(ndm), int(nch), int(S), int(G), _ptr(out))
+    if rc:
+        raise ValueError(f"hpo_subband_delays rc={rc}")
     return out
 
 
@@ -251,23 +267,26 @@ class SearchResult:
 
 
 def _params(nchans, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode, baseline_s,
-            dm_tol, t_gap, w_tol):
+            dm_tol, t_gap, w_tol, subband=None):
     dm = np.ascontiguousarray(dm_list, dtype=np.float32)
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p = _Params(int(nchans), float(f_top), float(chan_bw), float(tsamp),
                 dm.ctypes.data_as(_P(C.c_float)), int(dm.size), w.ctypes.data_as(_P(C.c_int32)),
                 int(w.size), float(thr), int(baseline_mode), float(baseline_s), int(dm_tol),
-                int(t_gap), int(w.size if w_tol is None else w_tol))
+                int(t_gap), int(w.size if w_tol is None else w_tol),
+                int(subband[0]) if subband else 0, int(subband[1]) if subband else 1)
     return p, (dm, w)
 
 
 def search(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode=0,
-           baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None, cap=1 << 22) -> SearchResult:
-    """The whole hot path on a uint8[nsamps][nchans] filterbank."""
+           baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None, cap=1 << 22,
+           subband=None) -> SearchResult:
+    """The whole hot path on a uint8[nsamps][nchans] filterbank.  subband=(S, G)
+    dedisperses with the sub-band variant's effective table (subband_delays)."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     nsamps, nch = x.shape
     p, keep = _params(nch, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode,
-                      baseline_s, dm_tol, t_gap, w_tol)
+                      baseline_s, dm_tol, t_gap, w_tol, subband)
     ndm = keep[0].size
     raw = np.empty(cap, dtype=RAW_DTYPE)
     cl = np.empty(cap, dtype=CLUSTER_DTYPE)

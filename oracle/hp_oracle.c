@@ -25,6 +25,8 @@
  *   hpo_mad               pinned: numpy sort median, Gaussian unit RMS
  *   hpo_detect_trial      pinned: naive window sums, rectangular pulse, brute-force runs
  *   hpo_merge             pinned: brute-force O(N^2) components, permutation invariance
+ *   hpo_subband_delays    pinned: two-stage brute force, S = 1 / G = 1 / S = nchans
+ *                                 reductions, closed-form error bound
  */
 #include <math.h>
 #include <stdint.h>
@@ -81,6 +83,40 @@ int32_t hpo_max_delay(const int32_t* delays, int ndm, int nchans) {
     for (int64_t i = 0; i < (int64_t)ndm * nchans; ++i)
         if (delays[i] > m) m = delays[i];
     return m;
+}
+
+/* ------------------------------------------------------------------------
+ * Variant of step c2 that the paper does not use: two-stage (sub-band)
+ * dedispersion, the classic way of trading sensitivity for work.  Channels
+ * are cut into sub-bands of S consecutive channels (sub-band s = c / S, its
+ * first, highest-frequency channel top(s) = s*S) and trials into groups of G
+ * consecutive trials (group g = d / G, of size len(g) = min(G, ndm - g*G))
+ * whose nominal trial is n(g) = g*G + (len(g) - 1) / 2.
+ *   stage 1, per sub-band and group:
+ *     B[s][g][u] = sum over c in s of x[u + delay(c,n(g)) - delay(top(s),n(g))][c]
+ *   stage 2, per trial:
+ *     D~[d][t]   = sum over s of B[s][g(d)][t + delay(top(s),d)]
+ * Putting stage 1 into stage 2, D~ is direct dedispersion (step c2) with the
+ * effective delay table
+ *     e(c,d) = delay(top(s),d) + delay(c,n(g(d))) - delay(top(s),n(g(d))),
+ * which this function writes; the variant's nout is nsamps - max e.  S = 1
+ * or G = 1 give e = delay; S >= nchans gives e(c,d) = delay(c,n(g(d))).
+ * ---------------------------------------------------------------------- */
+int hpo_subband_delays(const int32_t* delays /* [ndm][nchans] */, int ndm, int nchans,
+                       int S, int G, int32_t* out /* [ndm][nchans] */) {
+    if (ndm <= 0 || nchans <= 0 || S < 1 || G < 1) return HPO_ERR_ARG;
+    for (int d = 0; d < ndm; ++d) {
+        int g = d / G;
+        int len = ndm - g * G < G ? ndm - g * G : G;
+        int n = g * G + (len - 1) / 2;
+        const int32_t* at_d = delays + (int64_t)d * nchans;
+        const int32_t* at_n = delays + (int64_t)n * nchans;
+        for (int c = 0; c < nchans; ++c) {
+            int top = (c / S) * S;
+            out[(int64_t)d * nchans + c] = at_d[top] + at_n[c] - at_n[top];
+        }
+    }
+    return HPO_OK;
 }
 
 /* ------------------------------------------------------------------------
@@ -560,7 +596,23 @@ typedef struct {
     int dm_tol;
     int64_t t_gap;
     int w_tol;
+    int subband_chans;   /* S of the sub-band variant; 0 = direct dedispersion */
+    int subband_group;   /* G of the sub-band variant */
 } hpo_params;
+
+/* The delay table a search dedisperses with: step c1's, or the sub-band
+ * variant's effective table when subband_chans > 0. */
+static int search_delays(const hpo_params* p, int32_t* delays) {
+    int rc = hpo_delays(p->nchans, p->f_top, p->chan_bw, p->tsamp, p->dm_list, p->ndm, delays);
+    if (rc || p->subband_chans <= 0) return rc;
+    size_t n = (size_t)p->ndm * (size_t)p->nchans;
+    int32_t* e = (int32_t*)malloc(sizeof(int32_t) * n);
+    if (!e) return HPO_ERR_ARG;
+    rc = hpo_subband_delays(delays, p->ndm, p->nchans, p->subband_chans, p->subband_group, e);
+    if (!rc) memcpy(delays, e, sizeof(int32_t) * n);
+    free(e);
+    return rc;
+}
 
 int64_t hpo_baseline_window(double baseline_s, double tsamp) {
     return (int64_t)floor(baseline_s / tsamp + 0.5);
@@ -621,7 +673,7 @@ int hpo_search(const uint8_t* x, int64_t nsamps, const hpo_params* p,
     *ncl = 0;
     int32_t* delays = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->ndm * (size_t)p->nchans);
     if (!delays) return HPO_ERR_ARG;
-    int rc = hpo_delays(p->nchans, p->f_top, p->chan_bw, p->tsamp, p->dm_list, p->ndm, delays);
+    int rc = search_delays(p, delays);
     if (rc) { free(delays); return rc; }
     int32_t maxd = hpo_max_delay(delays, p->ndm, p->nchans);
     int wmax = 0;
@@ -657,7 +709,7 @@ int hpo_search_window(const uint8_t* x, int64_t nsamps, const hpo_params* p, int
     *ncl = 0;
     int32_t* delays = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->ndm * (size_t)p->nchans);
     if (!delays) return HPO_ERR_ARG;
-    int rc = hpo_delays(p->nchans, p->f_top, p->chan_bw, p->tsamp, p->dm_list, p->ndm, delays);
+    int rc = search_delays(p, delays);
     if (rc) { free(delays); return rc; }
     int32_t maxd = hpo_max_delay(delays, p->ndm, p->nchans);
     int wmax = 0;

@@ -56,10 +56,16 @@ MUTANTS = {
     "rfi_zero_dm_unmasked": ("acc += chan_flag[c] ? m[c] : x[t * nchans + c];",
                              "acc += x[t * nchans + c];"),
     "rfi_mad_from_raw": ("ha[v > m[c] ? v - m[c] : m[c] - v] += h[v];", "ha[v] += h[v];"),
+    # sub-band dedispersion variant
+    "subband_nominal_upper": ("int n = g * G + (len - 1) / 2;", "int n = g * G + len / 2;"),
+    "subband_top_index": ("int top = (c / S) * S;", "int top = c / S;"),
+    "subband_rel_at_trial": ("at_d[top] + at_n[c] - at_n[top]", "at_d[top] + at_d[c] - at_d[top]"),
+    "subband_no_stage2_shift": ("at_d[top] + at_n[c] - at_n[top]", "at_n[c]"),
 }
 
 # the pin files that each group of mutants is checked against
-PINS = {"rfi_": ["test_oracle_rfi.py"], "stream_": ["test_oracle_stream.py"]}
+PINS = {"rfi_": ["test_oracle_rfi.py"], "stream_": ["test_oracle_stream.py"],
+        "subband_": ["test_oracle_subband.py"]}
 DEFAULT_PINS = ["test_oracle_pins.py", "test_oracle_stream.py"]
 
 
