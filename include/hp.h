@@ -127,13 +127,32 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_RFI 9            /* 1 = RFI mitigation before dedispersion (default 0) */
 #define HP_PARAM_RFI_NB_K 10      /* narrowband threshold, integer >= 0 (default 5) */
 #define HP_PARAM_RFI_BB_K 11      /* broadband threshold in sigma of the zero-DM series (> 0, default 5) */
+/* Sub-band (two-stage) dedispersion, a variant the paper does not use: fewer
+ * additions per trial for a bounded loss of sensitivity.  With S =
+ * HP_PARAM_SUBBAND_CHANS > 0 the channels are cut into sub-bands of S
+ * consecutive channels (first channel top(s) = s*S) and the trials into groups
+ * of G = HP_PARAM_SUBBAND_GROUP consecutive trials with nominal trial
+ * n(g) = g*G + (len(g) - 1) / 2 (len(g) = the group's size).  Stage 1 sums each
+ * sub-band at each nominal trial, B[s][g][u] = sum over c in s of
+ * x[u + delay(c,n(g)) - delay(top(s),n(g))][c]; stage 2 sums, per trial, the
+ * shifted partial sums D~[d][t] = sum over s of B[s][g(d)][t + delay(top(s),d)].
+ * This equals direct dedispersion with the effective table
+ * e(c,d) = delay(top(s),d) + delay(c,n(g(d))) - delay(top(s),n(g(d))), which
+ * hp_plan_delays then returns (hp_plan_max_delay its maximum; nout = nsamps -
+ * that maximum).  hp_search, hp_dedisperse and hp_plan_autotune follow the
+ * variant (byte-row tile shapes only); batches and streams refuse it
+ * (HP_ERR_INVALID_ARG).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
+ * delay of channel c per unit DM in samples. */
+#define HP_PARAM_SUBBAND_CHANS 12 /* S: channels per sub-band, 0 = direct dedispersion (default) */
+#define HP_PARAM_SUBBAND_GROUP 13 /* G: trials per group, 1..ndm (default 8) */
 
 #define HP_NUM_DEDISP_CONFIGS 27
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);
 
-/* Copy the delay table, int32 [ndm][nchans] row-major, into host memory. */
+/* Copy the delay table, int32 [ndm][nchans] row-major, into host memory (the
+ * sub-band variant's effective table when HP_PARAM_SUBBAND_CHANS > 0). */
 int hp_plan_delays(const hp_plan* plan, int32_t* out_host);
 
 /* Largest delay of the table (samples) and the dedispersed length

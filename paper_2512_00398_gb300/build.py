@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhp.so")
-SOURCES = ["plan.cpp", "stream.cpp", "dedisp.cu", "search.cu", "rfi.cu", "merge.cu", "merge_static.cu", "peaks.cu"]
+SOURCES = ["plan.cpp", "stream.cpp", "dedisp.cu", "search.cu", "rfi.cu", "subband.cu", "merge.cu", "merge_static.cu", "peaks.cu"]
 HEADERS = ["common.cuh", "hp_internal.h", "plan_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

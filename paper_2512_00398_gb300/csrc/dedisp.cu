@@ -842,7 +842,9 @@ __device__ __forceinline__ uint32_t imad_add(uint32_t acc, uint32_t x, uint32_t 
     return r;
 }
 
-template <int RD, int NW, int WD, int WT, int NB, int UNR = 1>
+// SEG: the tile's stages form segments (sub-band stage 1); the sums are
+// written to rows seg_row + trial after the last stage of each segment.
+template <int RD, int NW, int WD, int WT, int NB, int UNR = 1, bool SEG = false>
 __global__ void __launch_bounds__(32 * (WD * WT + 1), 1)
 dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, int* status,
                    uint64_t timeout_ns, uint32_t one) {
@@ -936,6 +938,28 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
         }
     // byte offset of this lane's first word inside a staged row
     const uint32_t lane_off = 4u * (uint32_t)(wt * 32 * NW + NW * lane);
+    // the sums of trial dl go to row row0 + dl (samples t < nout)
+    auto write_rows = [&](int64_t row0) {
+#pragma unroll
+        for (int r = 0; r < RD; ++r) {
+            const int dl = wd * RD + r;
+            if (dl >= T.nd) continue;
+            int32_t* row = J.out + (row0 + dl) * J.out_pitch;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const int64_t t = t0 + wt * 128 * NW + 4 * (NW * lane + k);
+                if (t + 3 < J.nout) {
+                    *reinterpret_cast<int4*>(row + t) =
+                        make_int4((int)sum[r][k][0], (int)sum[r][k][1], (int)sum[r][k][2],
+                                  (int)sum[r][k][3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (t + e < J.nout) row[t + e] = (int)sum[r][k][e];
+                }
+            }
+        }
+    };
     uint32_t held = 0;
     for (int s = 0; s < nst; ++s) {
         const int b = s % NB;
@@ -980,8 +1004,9 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
         held += nchan;
+        const bool seg_end = SEG && S.seg_end != 0u;
         const uint32_t next_n = s + 1 < nst ? J.stages[T.stage_begin + s + 1].nchan : 256u;
-        if (held + next_n > 256u) {
+        if (seg_end || held + next_n > 256u) {
             held = 0;
 #pragma unroll
             for (int r = 0; r < RD; ++r)
@@ -995,36 +1020,26 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
                     acc_hi[r][k] = 0;
                 }
         }
-    }
-
+        if (seg_end) {
+            write_rows(S.seg_row);
 #pragma unroll
-    for (int r = 0; r < RD; ++r) {
-        const int dl = wd * RD + r;
-        if (dl >= T.nd) continue;
-        int32_t* row = J.out + (int64_t)(T.d0 + dl) * J.out_pitch;
+            for (int r = 0; r < RD; ++r)
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const int64_t t = t0 + wt * 128 * NW + 4 * (NW * lane + k);
-            if (t + 3 < J.nout) {
-                *reinterpret_cast<int4*>(row + t) =
-                    make_int4((int)sum[r][k][0], (int)sum[r][k][1], (int)sum[r][k][2],
-                              (int)sum[r][k][3]);
-            } else {
+                for (int k = 0; k < NW; ++k)
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (t + e < J.nout) row[t + e] = (int)sum[r][k][e];
-            }
+                    for (int e = 0; e < 4; ++e) sum[r][k][e] = 0;
         }
     }
+    if (!SEG) write_rows(T.d0);
 }
 
-template <int RD, int NW, int WD, int WT, int NB, int UNR = 1>
+template <int RD, int NW, int WD, int WT, int NB, int UNR = 1, bool SEG = false>
 cudaError_t run_dedisp_rows(const DedispBatch& b, int stage_bytes, int* status,
                             uint64_t timeout_ns, cudaStream_t s) {
     const int64_t total = b.prefix[b.njobs];
     if (total <= 0) return cudaSuccess;
     const size_t smem = (size_t)NB * stage_bytes + 2 * NB * 8;
-    auto k = dedisp_rows_kernel<RD, NW, WD, WT, NB, UNR>;
+    auto k = dedisp_rows_kernel<RD, NW, WD, WT, NB, UNR, SEG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)total, 32 * (WD * WT + 1), smem, s>>>(b, stage_bytes, status, timeout_ns, 1u);
@@ -1111,6 +1126,21 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
         case 24: return run_dedisp_rows<1, 7, 24, 1, 4, 2>(b, sb, status, timeout_ns, s);
         case 25: return run_dedisp_rows<1, 5, 30, 1, 4, 2>(b, sb, status, timeout_ns, s);
         case 26: return run_dedisp_rows<1, 7, 16, 1, 4, 2>(b, sb, status, timeout_ns, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool segmented_config(int cfg) { return cfg == 17 || cfg == 21 || cfg == 22 || cfg == 24; }
+
+cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& b, int* status,
+                                    uint64_t timeout_ns, cudaStream_t s) {
+    if (cfg < 0 || cfg >= kNumDedispConfigs) return cudaErrorInvalidValue;
+    const int sb = kDedispConfigs[cfg].stage_bytes;
+    switch (cfg) {
+        case 17: return run_dedisp_rows<2, 5, 8, 2, 4, 1, true>(b, sb, status, timeout_ns, s);
+        case 21: return run_dedisp_rows<2, 5, 12, 1, 4, 1, true>(b, sb, status, timeout_ns, s);
+        case 22: return run_dedisp_rows<2, 7, 12, 1, 4, 2, true>(b, sb, status, timeout_ns, s);
+        case 24: return run_dedisp_rows<1, 7, 24, 1, 4, 2, true>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

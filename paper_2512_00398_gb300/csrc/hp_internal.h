@@ -67,7 +67,13 @@ struct StageDesc {
     uint32_t tx_bytes;    // bytes landing in shared memory for this stage
     uint32_t addr_begin;  // index of the stage's table in the address array
     uint32_t addr_bytes;  // table bytes (pairs * BD * 8, layout 2: pairs * BD * 16)
+    // Segments (sub-band stage 1, byte-row kernel): the tile's channels are cut
+    // into segments that no stage straddles; after the last stage of a segment
+    // the block writes its sums to rows seg_row + trial and starts from zero.
+    int32_t seg_row;
+    uint32_t seg_end;     // 1 on the last stage of a segment
 };
+static_assert(sizeof(StageDesc) == 32, "StageDesc layout");
 
 struct TileDesc {
     int32_t d0, nd;            // first trial, trial count (<= BD)
@@ -138,6 +144,27 @@ cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8
                              int64_t xt_pitch, cudaStream_t s);
 cudaError_t launch_dedisp(int cfg, const DedispBatch& batch, int* status, uint64_t timeout_ns,
                           cudaStream_t s);
+// The same tilings run segment by segment (stage 1 of the sub-band variant):
+// rows are written at the end of every segment (StageDesc::seg_row / seg_end).
+// Byte-row configs for which segmented_config() holds only.
+bool segmented_config(int cfg);
+cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& batch, int* status,
+                                    uint64_t timeout_ns, cudaStream_t s);
+
+// Stage 2 of the sub-band variant: for trials d in [d_begin, d_end),
+// out[d][t] = sum over sub-bands s of B[row(d, s)][t + top[d][s]], t < nout,
+// with row(d, s) = ((g / gchunk - c0) * nsub + s) * gchunk + g % gchunk, g = d / G.
+struct SubbandArgs {
+    const int32_t* B;
+    int64_t bpitch;
+    const int32_t* top;        // [ndm][nsub] delay of each sub-band's first channel
+    int32_t nsub, G, gchunk, c0;
+    int32_t d_begin, d_end;
+    int32_t* out;
+    int64_t out_pitch;
+    int64_t nout;
+};
+cudaError_t launch_subband_sum(const SubbandArgs& a, cudaStream_t s);
 TransposeJob make_transpose_job(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
                                 int64_t xt_pitch);
 cudaError_t launch_transpose_batch(const TransposeBatch& tb, cudaStream_t s);

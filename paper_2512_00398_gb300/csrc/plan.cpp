@@ -21,10 +21,15 @@ constexpr double kKDM = 4148.808;   // s MHz^2 pc^-1 cm^3
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int64_t round_up64(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+// bytes of sub-band partial sums held at once (chunks of DM tiles are run in
+// turn when all of them would need more)
+constexpr size_t kSubbandBytes = (size_t)16 << 30;
 
 }  // namespace
 
 namespace hp {
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int check_cuda(cudaError_t e) {
     if (e == cudaSuccess) return HP_OK;
@@ -107,10 +112,9 @@ struct RowGeom {
     uint32_t nwords, bbytes, smem;
 };
 
-RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT, int layout) {
+// lo / hi: the smallest and largest delay of channel c over the tile's trials
+RowGeom row_geom_span(int32_t lo, int32_t hi, int BT, int layout) {
     RowGeom g;
-    const int32_t lo = p->delays[(size_t)d0 * p->nchans + c];
-    const int32_t hi = p->delays[(size_t)(d0 + nd - 1) * p->nchans + c];
     g.base = lo & ~15;
     const uint32_t span = (uint32_t)(hi - g.base);
     if (layout == 0) {
@@ -134,6 +138,12 @@ RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT, int layout) {
     return g;
 }
 
+// direct tables grow with the trial index, so the first and last trial bound a channel
+RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT, int layout) {
+    return row_geom_span(p->delays[(size_t)d0 * p->nchans + c],
+                         p->delays[(size_t)(d0 + nd - 1) * p->nchans + c], BT, layout);
+}
+
 // Table entries per channel pair and trial: two 32-bit words (layouts 0, 1:
 // byte offsets) or four (layout 2: byte offsets and PRMT selectors).
 uint32_t stage_table_bytes(int nchan, int BD, int layout) {
@@ -146,44 +156,40 @@ uint32_t stage_header(int nchan, int BD, int layout) {
                       align_up(stage_table_bytes(nchan, BD, layout), 16));
 }
 
-int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
-    const DedispConfig& C = kDedispConfigs[cfg];
+// Stages, channel descriptors and address tables of one DM tile of nd trials
+// whose delay of trial j in channel c is delay(j, c); channels [0, nch) are
+// cut at seg_begin[i] into segments that no stage straddles, the trials of
+// segment i being written to rows seg_row[i] + j.
+template <class Delay>
+int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg_begin,
+                const std::vector<int32_t>& seg_row, int32_t d0, const DedispConfig& C,
+                DedispTiling* T) {
     const int BD = C.BD(), BT = C.BT();
     const uint32_t budget = (uint32_t)C.stage_bytes;
-    const int ndm = p->ndm(), nch = p->nchans;
-    T->cfg = cfg;
-    T->BD = BD;
-    T->BT = BT;
-    T->tiles.clear();
-    T->stages.clear();
-    T->chans.clear();
-    T->addr.clear();
-    T->max_reach = 0;
-    int d0 = 0;
-    while (d0 < ndm) {
-        // grow the tile while every channel row alone still fits a stage
-        int nd = 1;
-        while (nd < BD && d0 + nd < ndm) {
-            bool ok = true;
-            for (int c = nch - 1; c >= 0 && ok; --c)
-                ok = row_geom(p, d0, nd + 1, c, BT, C.layout).smem + stage_header(1, BD, C.layout) <= budget;
-            if (!ok) break;
-            ++nd;
+    std::vector<RowGeom> geo_all(nch);
+    for (int c = 0; c < nch; ++c) {
+        int32_t lo = delay(0, c), hi = lo;
+        for (int j = 1; j < nd; ++j) {
+            lo = std::min(lo, delay(j, c));
+            hi = std::max(hi, delay(j, c));
         }
-        for (int c = 0; c < nch; ++c)
-            if (row_geom(p, d0, nd, c, BT, C.layout).smem + stage_header(1, BD, C.layout) > budget)
-                return HP_ERR_INVALID_ARG;
-        TileDesc td;
-        td.d0 = d0;
-        td.nd = nd;
-        td.stage_begin = (int32_t)T->stages.size();
-        td.nstages = 0;
-        int c = 0;
-        while (c < nch) {
+        geo_all[c] = row_geom_span(lo, hi, BT, C.layout);
+        if (geo_all[c].smem + stage_header(1, BD, C.layout) > budget) return HP_ERR_INVALID_ARG;
+    }
+    TileDesc td;
+    td.d0 = d0;
+    td.nd = nd;
+    td.stage_begin = (int32_t)T->stages.size();
+    td.nstages = 0;
+    const int nseg = (int)seg_begin.size();
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int c_end = sg + 1 < nseg ? seg_begin[sg + 1] : nch;
+        int c = seg_begin[sg];
+        while (c < c_end) {
             int n = 0;
             uint32_t rows = 0;
-            while (c + n < nch && n < kStageMaxChans) {
-                const RowGeom g = row_geom(p, d0, nd, c + n, BT, C.layout);
+            while (c + n < c_end && n < kStageMaxChans) {
+                const RowGeom& g = geo_all[c + n];
                 if (stage_header(n + 1, BD, C.layout) + rows + g.smem > budget) break;
                 rows += g.smem;
                 ++n;
@@ -194,17 +200,16 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             sd.addr_off = (uint32_t)align_up((size_t)n * sizeof(ChanDesc), 16);
             sd.addr_begin = (uint32_t)T->addr.size();
             sd.addr_bytes = stage_table_bytes(n, BD, C.layout);
+            sd.seg_row = seg_row[sg];
+            sd.seg_end = c + n == c_end ? 1u : 0u;
             uint32_t off = stage_header(n, BD, C.layout);
             uint32_t tx = (uint32_t)(n * sizeof(ChanDesc)) + sd.addr_bytes;
             std::vector<uint32_t> word0(n);   // per channel: byte offset of row copy 0
-            std::vector<RowGeom> geo(n);
             for (int i = 0; i < n; ++i) {
-                const int cc = c + i;
-                const RowGeom g = row_geom(p, d0, nd, cc, BT, C.layout);
-                geo[i] = g;
+                const RowGeom& g = geo_all[c + i];
                 word0[i] = off;
                 ChanDesc cd;
-                cd.c = (uint32_t)cc;
+                cd.c = (uint32_t)(c + i);
                 cd.goff = g.base;
                 cd.offB = off;
                 cd.nwords = g.nwords;
@@ -223,8 +228,8 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                         const int i = 2 * pr + e < n ? 2 * pr + e : 2 * pr;
                         const int cc = c + i;
                         const int jj = j < nd ? j : 0;
-                        const RowGeom& g = geo[i];
-                        const int32_t rel = p->delays[(size_t)(d0 + jj) * nch + cc] - g.base;
+                        const RowGeom& g = geo_all[cc];
+                        const int32_t rel = delay(jj, cc) - g.base;
                         const uint32_t offV = word0[i] + g.bbytes;
                         if (C.layout == 2) {
                             // the row's word rel >> 2; bytes rel & 3 .. 3 + (rel & 3)
@@ -254,10 +259,115 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
             td.nstages++;
             c += n;
         }
-        T->tiles.push_back(td);
+    }
+    T->tiles.push_back(td);
+    return HP_OK;
+}
+
+// The nominal trial of the group of trial d (sub-band variant): the lower
+// middle trial of the group.
+int sb_nominal(const hp_plan* p, int d) {
+    const int G = p->sb_group, g = d / G;
+    const int len = std::min(G, p->ndm() - g * G);
+    return g * G + (len - 1) / 2;
+}
+
+int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
+    const DedispConfig& C = kDedispConfigs[cfg];
+    const int BD = C.BD(), BT = C.BT();
+    const uint32_t budget = (uint32_t)C.stage_bytes;
+    const int ndm = p->ndm(), nch = p->nchans;
+    T->cfg = -1;   // set once the tiling is complete
+    T->BD = BD;
+    T->BT = BT;
+    T->tiles.clear();
+    T->stages.clear();
+    T->chans.clear();
+    T->addr.clear();
+    T->max_reach = 0;
+    if (p->sb_chans > 0) {
+        // Sub-band stage 1: one tile per chunk of BD groups; its trial j is the
+        // nominal trial of group g0 + j, each sub-band a segment whose delays
+        // are taken relative to the sub-band's first channel, written to rows
+        // s * BD + j of the chunk's partial-sum block.
+        if (!segmented_config(cfg)) return HP_ERR_INVALID_ARG;
+        const int S = p->sb_chans;
+        std::vector<int> seg_begin;
+        std::vector<int32_t> seg_row;
+        for (int s = 0; s < p->sb_nsub; ++s) {
+            seg_begin.push_back(s * S);
+            seg_row.push_back(s * BD);
+        }
+        for (int g0 = 0; g0 < p->sb_ngrp; g0 += BD) {
+            const int nd = std::min(BD, p->sb_ngrp - g0);
+            auto delay = [&](int j, int c) {
+                const int32_t* row = &p->delays[(size_t)sb_nominal(p, (g0 + j) * p->sb_group) * nch];
+                return row[c] - row[(c / S) * S];
+            };
+            const int rc = append_tile(delay, nd, nch, seg_begin, seg_row, 0, C, T);
+            if (rc) return rc;
+        }
+        T->cfg = cfg;
+        return HP_OK;
+    }
+    int d0 = 0;
+    while (d0 < ndm) {
+        // grow the tile while every channel row alone still fits a stage
+        int nd = 1;
+        while (nd < BD && d0 + nd < ndm) {
+            bool ok = true;
+            for (int c = nch - 1; c >= 0 && ok; --c)
+                ok = row_geom(p, d0, nd + 1, c, BT, C.layout).smem + stage_header(1, BD, C.layout) <= budget;
+            if (!ok) break;
+            ++nd;
+        }
+        const int32_t* base = &p->delays[(size_t)d0 * nch];
+        auto delay = [&](int j, int c) { return base[(size_t)j * nch + c]; };
+        const int rc = append_tile(delay, nd, nch, {0}, {d0}, d0, C, T);
+        if (rc) return rc;
         d0 += nd;
     }
+    T->cfg = cfg;
     return HP_OK;
+}
+
+// The table the dedispersion realises: the direct one, or the sub-band
+// variant's effective table e(c,d) = delay(top,d) + delay(c,n) - delay(top,n)
+// (top = the sub-band's first channel, n = the nominal trial of d's group),
+// with the extents its two stages need.  Drops the tiling and device tables.
+void apply_subband(hp_plan* p) {
+    const int ndm = p->ndm(), nch = p->nchans;
+    p->tiling.cfg = -1;
+    int32_t mx = 0;
+    if (p->sb_chans <= 0) {
+        std::vector<int32_t>().swap(p->sb_eff);
+        for (int32_t v : p->delays) mx = std::max(mx, v);
+        p->maxd = mx;
+        p->sb_nsub = p->sb_ngrp = 0;
+        p->sb_maxrel = p->sb_maxtop = 0;
+        return;
+    }
+    const int S = p->sb_chans;
+    p->sb_nsub = (int32_t)ceil_div(nch, S);
+    p->sb_ngrp = (int32_t)ceil_div(ndm, p->sb_group);
+    p->sb_eff.assign((size_t)ndm * nch, 0);
+    int32_t maxrel = 0, maxtop = 0;
+    for (int d = 0; d < ndm; ++d) {
+        const int32_t* at_d = &p->delays[(size_t)d * nch];
+        const int32_t* at_n = &p->delays[(size_t)sb_nominal(p, d) * nch];
+        int32_t* e = &p->sb_eff[(size_t)d * nch];
+        for (int c = 0; c < nch; ++c) {
+            const int top = (c / S) * S;
+            const int32_t rel = at_n[c] - at_n[top];
+            e[c] = at_d[top] + rel;
+            mx = std::max(mx, e[c]);
+            maxrel = std::max(maxrel, rel);
+            maxtop = std::max(maxtop, at_d[top]);
+        }
+    }
+    p->maxd = mx;
+    p->sb_maxrel = maxrel;
+    p->sb_maxtop = maxtop;
 }
 
 // ------------------------------------------------------------- workspace
@@ -267,7 +377,6 @@ int64_t xt_pitch_for(int64_t nsamps) {
     return round_up64(nsamps + bt_max + 32, 16);
 }
 
-int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int64_t baseline_window(const hp_plan* p) {
     return (int64_t)std::floor(p->baseline_s / p->tsamp + 0.5);
@@ -295,10 +404,23 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
         return at;
     };
     if (with_dedisp) {
-        L.xt_pitch = xt_pitch_for(nsamps);
+        // stage 1 of the sub-band variant reads up to sb_maxrel samples past
+        // the last sample a result uses
+        L.xt_pitch = xt_pitch_for(nsamps + (p->sb_chans > 0 ? p->sb_maxrel : 0));
         L.dpitch = round_up64(L.nout, 64);
         L.xt = take((size_t)p->nchans * L.xt_pitch);
         L.D = take((size_t)ndm * L.dpitch * 4);
+        if (p->sb_chans > 0 && L.nout > 0) {
+            // partial sums B of whole chunks of BD groups: nsub * BD rows per chunk
+            const int64_t BD = kDedispConfigs[p->dedisp_cfg].BD();
+            const int64_t nchunks = ceil_div(p->sb_ngrp, BD);
+            L.sb_len = L.nout + p->sb_maxtop;
+            L.sb_pitch = round_up64(L.sb_len, 64);
+            const size_t chunk = (size_t)p->sb_nsub * BD * L.sb_pitch * 4;
+            L.sb_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(
+                {nchunks, (int64_t)kMaxJobs, (int64_t)(kSubbandBytes / chunk)}));
+            L.sb = take(chunk * L.sb_chunks);
+        }
     }
     // RFI stage (small: per-channel counts and one int32 series of nsamps)
     {
@@ -389,7 +511,8 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
 }
 
 int ensure_device_tables(hp_plan* p) {
-    if (p->tables && p->tables_cfg == p->dedisp_cfg) return HP_OK;
+    const int64_t sb_key = p->sb_chans > 0 ? ((int64_t)p->sb_chans << 32) | p->sb_group : 0;
+    if (p->tables && p->tables_cfg == p->dedisp_cfg && p->tables_sb == sb_key) return HP_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HP_ERR_CUDA;
     if (p->tiling.cfg != p->dedisp_cfg) {
@@ -409,6 +532,16 @@ int ensure_device_tables(hp_plan* p) {
     const size_t o_chans = take(T.chans.size() * sizeof(ChanDesc));
     const size_t o_addr = take(T.addr.size() * sizeof(uint32_t));
     const size_t o_widths = take(p->widths.size() * sizeof(int32_t));
+    // sub-band variant: delay of every sub-band's first channel per trial
+    std::vector<int32_t> sbtop;
+    if (p->sb_chans > 0) {
+        sbtop.resize((size_t)p->ndm() * p->sb_nsub);
+        for (int d = 0; d < p->ndm(); ++d)
+            for (int sb = 0; sb < p->sb_nsub; ++sb)
+                sbtop[(size_t)d * p->sb_nsub + sb] =
+                    p->delays[(size_t)d * p->nchans + (size_t)sb * p->sb_chans];
+    }
+    const size_t o_sbtop = take(sbtop.size() * sizeof(int32_t));
     const size_t total = off;
     int prev_status = p->pending_status;
     p->pending_status = 0;
@@ -428,6 +561,8 @@ int ensure_device_tables(hp_plan* p) {
     std::memcpy(host.data() + o_chans, T.chans.data(), T.chans.size() * sizeof(ChanDesc));
     std::memcpy(host.data() + o_addr, T.addr.data(), T.addr.size() * sizeof(uint32_t));
     std::memcpy(host.data() + o_widths, p->widths.data(), p->widths.size() * sizeof(int32_t));
+    if (!sbtop.empty())
+        std::memcpy(host.data() + o_sbtop, sbtop.data(), sbtop.size() * sizeof(int32_t));
     rc = check_cuda(cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice));
     if (rc) {
         plan_free(p, mem, total);
@@ -437,6 +572,7 @@ int ensure_device_tables(hp_plan* p) {
     p->tables = mem;
     p->tables_bytes = total;
     p->tables_cfg = p->dedisp_cfg;
+    p->tables_sb = sb_key;
     p->device = dev;
     p->status = (int*)(b + o_status);
     p->d_tiles = (const TileDesc*)(b + o_tiles);
@@ -444,6 +580,7 @@ int ensure_device_tables(hp_plan* p) {
     p->d_chans = (const ChanDesc*)(b + o_chans);
     p->d_addr = (const uint32_t*)(b + o_addr);
     p->d_widths = (int32_t*)(b + o_widths);
+    p->d_sbtop = sbtop.empty() ? nullptr : (const int32_t*)(b + o_sbtop);
     return HP_OK;
 }
 
@@ -493,21 +630,77 @@ DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_
     return J;
 }
 
-int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, uint8_t* xt, int64_t xt_pitch,
-               int32_t* out, int64_t out_pitch, cudaStream_t s, const Layout* rfi_L = nullptr,
-               uint8_t* rfi_ws = nullptr) {
+// Stages 1 and 2 of the sub-band variant on the transposed input: per chunk
+// set, one segmented byte-row launch (partial sums of every sub-band at the
+// nominal trials of BD groups per chunk) and one sum launch (per trial, the
+// shifted partial sums of every sub-band).
+int run_subband(hp_plan* p, const Layout& L, uint8_t* ws, int32_t* out, int64_t out_pitch,
+                cudaStream_t s) {
+    const DedispTiling& T = p->tiling;
+    const int nchunks = (int)T.tiles.size();
+    const int64_t rows = (int64_t)p->sb_nsub * T.BD;     // partial-sum rows per chunk
+    int32_t* B = (int32_t*)(ws + L.sb);
+    if (!reach_ok(p, L.sb_len, L.xt_pitch)) return HP_ERR_INVALID_ARG;
+    for (int c0 = 0; c0 < nchunks; c0 += L.sb_chunks) {
+        const int n = std::min(L.sb_chunks, nchunks - c0);
+        DedispBatch db;
+        std::memset(&db, 0, sizeof(db));
+        db.njobs = n;
+        for (int k = 0; k < n; ++k) {
+            DedispJob J = make_job(p, ws + L.xt, L.xt_pitch, B + (size_t)k * rows * L.sb_pitch,
+                                   L.sb_pitch, L.sb_len);
+            J.tiles = p->d_tiles + (c0 + k);
+            J.ndt = 1;
+            db.jobs[k] = J;
+            db.prefix[k + 1] = db.prefix[k] + (int64_t)J.ntt * J.ndt;
+        }
+        int rc = check_cuda(launch_dedisp_segmented(p->dedisp_cfg, db, p->status, p->timeout_ns, s));
+        if (rc) return rc;
+        ++p->launches;
+        SubbandArgs a;
+        a.B = B;
+        a.bpitch = L.sb_pitch;
+        a.top = p->d_sbtop;
+        a.nsub = p->sb_nsub;
+        a.G = p->sb_group;
+        a.gchunk = T.BD;
+        a.c0 = c0;
+        a.d_begin = (int32_t)std::min<int64_t>((int64_t)c0 * T.BD * p->sb_group, p->ndm());
+        a.d_end = (int32_t)std::min<int64_t>((int64_t)(c0 + n) * T.BD * p->sb_group, p->ndm());
+        a.out = out;
+        a.out_pitch = out_pitch;
+        a.nout = L.nout;
+        rc = check_cuda(launch_subband_sum(a, s));
+        if (rc) return rc;
+        ++p->launches;
+    }
+    return HP_OK;
+}
+
+// Transpose, optional RFI mitigation, dedispersion (direct or sub-band) of one
+// input into out[ndm][out_pitch].
+int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, const Layout& L, uint8_t* ws,
+               int32_t* out, int64_t out_pitch, cudaStream_t s, bool with_rfi) {
+    uint8_t* xt = ws + L.xt;
+    const int64_t xt_pitch = L.xt_pitch;
     const int64_t nout = nsamps - p->maxd;
     int ti = stage_begin(p, HP_STAGE_TRANSPOSE, s);
     int rc = check_cuda(launch_transpose(fb, nsamps, p->nchans, xt, xt_pitch, s));
     stage_end(p, HP_STAGE_TRANSPOSE, ti, s);
     if (rc) return rc;
     ++p->launches;
-    if (p->rfi && rfi_ws) {
-        const RfiArgs r = make_rfi_args(p, *rfi_L, rfi_ws, fb, xt, xt_pitch, nsamps, nullptr);
+    if (p->rfi && with_rfi) {
+        const RfiArgs r = make_rfi_args(p, L, ws, fb, xt, xt_pitch, nsamps, nullptr);
         ti = stage_begin(p, HP_STAGE_RFI, s);
         rc = check_cuda(launch_rfi(r, s, &p->launches));
         stage_end(p, HP_STAGE_RFI, ti, s);
         if (rc) return rc;
+    }
+    if (p->sb_chans > 0) {
+        ti = stage_begin(p, HP_STAGE_DEDISP, s);
+        rc = run_subband(p, L, ws, out, out_pitch, s);
+        stage_end(p, HP_STAGE_DEDISP, ti, s);
+        return rc;
     }
     DedispBatch B;   // copied into the kernel parameters at launch
     std::memset(&B, 0, sizeof(B));
@@ -684,10 +877,10 @@ int time_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, cudaStream_t s, i
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return HP_ERR_CUDA; }
     const bool timing = p->timing;
     p->timing = false;
-    rc = run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, s);
+    rc = run_dedisp(p, fb, nsamps, L, ws, (int32_t*)(ws + L.D), L.dpitch, s, false);
     if (!rc) rc = check_cuda(cudaEventRecord(e0, s));
     for (int r = 0; r < reps && !rc; ++r)
-        rc = run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, s);
+        rc = run_dedisp(p, fb, nsamps, L, ws, (int32_t*)(ws + L.D), L.dpitch, s, false);
     if (!rc) rc = check_cuda(cudaEventRecord(e1, s));
     if (!rc) rc = check_cuda(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -733,6 +926,7 @@ int batch_prepare(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         hp_plan* p = b->plans[i];
         int rc = validate_search_input(p, fbs ? fbs[i] : nullptr, nsamps[i]);
         if (rc) return rc;
+        if (p->sb_chans > 0) return HP_ERR_INVALID_ARG;   // direct dedispersion only
         p->dedisp_cfg = b->cfg;
         rc = ensure_device_tables(p);
         if (rc) return rc;
@@ -962,6 +1156,16 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
             if (!(v > 0.0) || v > 1e6) return HP_ERR_INVALID_ARG;
             p->rfi_bb_k = (float)v;
             return HP_OK;
+        case HP_PARAM_SUBBAND_CHANS:
+            if (v < 0 || v > p->nchans || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->sb_chans = (int)v;
+            apply_subband(p);
+            return HP_OK;
+        case HP_PARAM_SUBBAND_GROUP:
+            if (v < 1 || v > p->ndm() || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            p->sb_group = (int)v;
+            apply_subband(p);
+            return HP_OK;
         default:
             return HP_ERR_INVALID_ARG;
     }
@@ -982,13 +1186,16 @@ int hp_plan_get_param(const hp_plan* p, int param, double* v) {
         case HP_PARAM_RFI: *v = p->rfi ? 1.0 : 0.0; return HP_OK;
         case HP_PARAM_RFI_NB_K: *v = p->rfi_nb_k; return HP_OK;
         case HP_PARAM_RFI_BB_K: *v = (double)p->rfi_bb_k; return HP_OK;
+        case HP_PARAM_SUBBAND_CHANS: *v = p->sb_chans; return HP_OK;
+        case HP_PARAM_SUBBAND_GROUP: *v = p->sb_group; return HP_OK;
         default: return HP_ERR_INVALID_ARG;
     }
 }
 
 int hp_plan_delays(const hp_plan* p, int32_t* out_host) {
     if (!p || !out_host) return HP_ERR_INVALID_ARG;
-    std::memcpy(out_host, p->delays.data(), p->delays.size() * sizeof(int32_t));
+    const std::vector<int32_t>& t = p->sb_chans > 0 ? p->sb_eff : p->delays;
+    std::memcpy(out_host, t.data(), t.size() * sizeof(int32_t));
     return HP_OK;
 }
 
@@ -1077,8 +1284,7 @@ int hp_dedisperse(hp_plan* p, const uint8_t* fb, int64_t nsamps, int32_t* out, i
     uint8_t* ws = nullptr;
     rc = ensure_workspace(p, L.total, &ws);
     if (rc) return rc;
-    return run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, out, pitch, (cudaStream_t)stream, &L,
-                      ws);
+    return run_dedisp(p, fb, nsamps, L, ws, out, pitch, (cudaStream_t)stream, true);
 }
 
 int hp_detect(hp_plan* p, const int32_t* series, int64_t nout, int64_t pitch, void* stream,
@@ -1141,7 +1347,7 @@ int hp_search(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream, hp_ca
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t* D = (int32_t*)(ws + L.D);
-    rc = run_dedisp(p, fb, nsamps, ws + L.xt, L.xt_pitch, D, L.dpitch, s, &L, ws);
+    rc = run_dedisp(p, fb, nsamps, L, ws, D, L.dpitch, s, true);
     if (rc) return rc;
     hp_raw_cand* raw = (hp_raw_cand*)(ws + L.raw);
     int64_t* raw_count = (int64_t*)(ws + L.raw_count);

@@ -28,6 +28,9 @@ struct Layout {
            r_lvl_a = 0, r_lvl_b = 0, r_mean = 0, r_zhist = 0, r_bucket = 0, r_rank = 0,
            r_mad = 0, r_sigma = 0, r_tint = 0, r_y = 0;
     int64_t r_zpitch = 0, r_lvl_pitch_a = 0, r_lvl_pitch_b = 0, r_mean_pitch = 0;
+    size_t sb = 0;             // sub-band partial sums (sub-band variant)
+    int64_t sb_pitch = 0, sb_len = 0;
+    int sb_chunks = 0;         // DM-tile chunks whose partial sums fit `sb` at once
     size_t y = 0;              // baseline-subtracted series (unless it overwrites D)
     int64_t ypitch = 0;
     bool y_in_D = false;
@@ -53,7 +56,16 @@ struct hp_plan {
     uint64_t timeout_ns = 1000000000ull;
 
     std::vector<int32_t> delays;   // [ndm][nchans]
-    int32_t maxd = 0, wmax = 0;
+    int32_t maxd = 0, wmax = 0;    // maxd: of the table the dedispersion realises
+
+    // sub-band variant (sb_chans > 0): sub-bands of sb_chans channels, groups of
+    // sb_group trials; sb_eff is the effective table [ndm][nchans]
+    int sb_chans = 0, sb_group = 8;
+    std::vector<int32_t> sb_eff;
+    int32_t sb_nsub = 0, sb_ngrp = 0, sb_gchunk = 0, sb_nchunks = 0;
+    int32_t sb_maxrel = 0;         // largest in-sub-band delay at a nominal trial
+    int32_t sb_maxtop = 0;         // largest delay of a sub-band's first channel
+    const int32_t* d_sbtop = nullptr;
 
     hp::DedispTiling tiling;           // for dedisp_cfg
 
@@ -62,6 +74,7 @@ struct hp_plan {
     void* tables = nullptr;        // plan-owned constant tables + status word
     size_t tables_bytes = 0;
     int tables_cfg = -1;
+    int64_t tables_sb = -1;        // (sb_chans, sb_group) the tables were built for
     int* status = nullptr;
     const hp::TileDesc* d_tiles = nullptr;
     const hp::StageDesc* d_stages = nullptr;

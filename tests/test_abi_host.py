@@ -171,3 +171,41 @@ def test_rfi_params():
     for name, bad in (("rfi", 2), ("rfi_nb_k", -1), ("rfi_nb_k", 2.5), ("rfi_bb_k", 0.0)):
         with pytest.raises(hp.HPError):
             plan.set_param(name, bad)
+
+
+@pytest.mark.parametrize("S,G", [(1, 8), (64, 1), (64, 8), (48, 5), (4096, 3), (100, 7)])
+def test_subband_table_matches_oracle(S, G):
+    """The plan's effective table of the sub-band variant (host code, no GPU)
+    equals the oracle's, and the maximum delay and nout follow it."""
+    w = workloads.fast(nsamps=1 << 17)
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold) as p:
+        direct = p.delays()
+        p.set_param("subband_chans", S)
+        p.set_param("subband_group", G)
+        want = oracle.subband_delays(direct, S, G)
+        assert np.array_equal(p.delays(), want)
+        assert p.max_delay == int(want.max())
+        assert p.nout(1 << 20) == (1 << 20) - int(want.max())
+        p.set_param("subband_chans", 0)                 # back to direct dedispersion
+        assert np.array_equal(p.delays(), direct) and p.max_delay == int(direct.max())
+
+
+def test_subband_params_and_workspace():
+    w = workloads.fast(nsamps=1 << 20)
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
+        assert p.get_param("subband_chans") == 0 and p.get_param("subband_group") == 8
+        direct_ws = p.workspace_bytes(1 << 20)
+        for name, bad in (("subband_chans", -1), ("subband_chans", o.nchans + 1),
+                          ("subband_chans", 2.5), ("subband_group", 0),
+                          ("subband_group", w.ndm + 1)):
+            with pytest.raises(hp.HPError):
+                p.set_param(name, bad)
+        p.set_param("subband_chans", 64)
+        p.set_param("subband_group", 8)
+        ws = p.workspace_bytes(1 << 20)
+        # partial sums: 64 sub-bands x 24 nominal trials per chunk, 2 chunks at once (< 16 GiB)
+        nb = p.nout(1 << 20) + int(p.delays()[:, ::64].max())
+        assert ws - direct_ws >= 2 * 64 * 24 * nb * 4
+        assert ws < direct_ws + (16 << 30) + (1 << 30)
