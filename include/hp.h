@@ -293,7 +293,8 @@ int hp_batch_kernels_per_call(const hp_batch* batch, int64_t* kernels);
 #define HP_STAGE_SEARCH 2       /* baseline, sigma, boxcars, peaks */
 #define HP_STAGE_MERGE 3        /* sort + friends-of-friends */
 #define HP_STAGE_RFI 4          /* RFI mitigation (when HP_PARAM_RFI = 1) */
-#define HP_NUM_STAGES 5
+#define HP_STAGE_SUBBAND_SUM 5  /* sub-band variant, stage 2 (stage 1 counts as HP_STAGE_DEDISP) */
+#define HP_NUM_STAGES 6
 typedef struct {
     double stage_ms[HP_NUM_STAGES];      /* summed event time of the recorded launches */
     int64_t stage_calls[HP_NUM_STAGES];  /* launches whose events were summed */

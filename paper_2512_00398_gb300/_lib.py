@@ -39,8 +39,9 @@ HP_PARAM_SUBBAND_GROUP = 13
 HP_NUM_DEDISP_CONFIGS = 27
 
 HP_STAGE_TRANSPOSE, HP_STAGE_DEDISP, HP_STAGE_SEARCH, HP_STAGE_MERGE, HP_STAGE_RFI = 0, 1, 2, 3, 4
-HP_NUM_STAGES = 5
-STAGE_NAMES = ("transpose", "dedisp", "search", "merge", "rfi")
+HP_STAGE_SUBBAND_SUM = 5
+HP_NUM_STAGES = 6
+STAGE_NAMES = ("transpose", "dedisp", "search", "merge", "rfi", "subband_sum")
 
 #: hp_cand (48 bytes)
 CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("width_idx", "<i4"), ("sample", "<i8"),

@@ -151,18 +151,25 @@ bool segmented_config(int cfg);
 cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& batch, int* status,
                                     uint64_t timeout_ns, cudaStream_t s);
 
-// Stage 2 of the sub-band variant: for trials d in [d_begin, d_end),
-// out[d][t] = sum over sub-bands s of B[row(d, s)][t + top[d][s]], t < nout,
-// with row(d, s) = ((g / gchunk - c0) * nsub + s) * gchunk + g % gchunk, g = d / G.
+// Stage 2 of the sub-band variant: for the trials d of groups [g_begin, g_end),
+// out[d][t] = sum over sub-bands s of B[row(g, s)][t + top[d][s]], t < nout,
+// with row(g, s) = ((g / gchunk - c0) * nsub + s) * gchunk + g % gchunk, g = d / G.
+// A block takes up to kSubbandTrials trials of one group and one time tile;
+// win_cap (int32 per staged window, a multiple of 4) must hold the tile plus
+// the largest spread top[d_last][s] - top[d_first][s] of a block, plus 8.
+constexpr int kSubbandTrials = 8;
+constexpr int kSubbandTile = 2048;       // output samples per block
 struct SubbandArgs {
     const int32_t* B;
-    int64_t bpitch;
+    int64_t bpitch;            // int32 per row, a multiple of 4
     const int32_t* top;        // [ndm][nsub] delay of each sub-band's first channel
     int32_t nsub, G, gchunk, c0;
-    int32_t d_begin, d_end;
+    int32_t g_begin, g_end, ndm, win_cap;
     int32_t* out;
     int64_t out_pitch;
     int64_t nout;
+    int* status;
+    uint64_t timeout_ns;
 };
 cudaError_t launch_subband_sum(const SubbandArgs& a, cudaStream_t s);
 TransposeJob make_transpose_job(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,

@@ -344,7 +344,7 @@ void apply_subband(hp_plan* p) {
         for (int32_t v : p->delays) mx = std::max(mx, v);
         p->maxd = mx;
         p->sb_nsub = p->sb_ngrp = 0;
-        p->sb_maxrel = p->sb_maxtop = 0;
+        p->sb_maxrel = p->sb_maxtop = p->sb_spread = 0;
         return;
     }
     const int S = p->sb_chans;
@@ -368,6 +368,16 @@ void apply_subband(hp_plan* p) {
     p->maxd = mx;
     p->sb_maxrel = maxrel;
     p->sb_maxtop = maxtop;
+    // stage 2 stages, per sub-band, the window its block's trials read: the
+    // spread of the sub-band's first-channel delay over the block's trials
+    int32_t spread = 0;
+    for (int g = 0; g < p->sb_ngrp; ++g)
+        for (int d0 = g * p->sb_group; d0 < std::min((g + 1) * p->sb_group, ndm); d0 += kSubbandTrials) {
+            const int d1 = std::min({d0 + kSubbandTrials, (g + 1) * p->sb_group, ndm}) - 1;
+            for (int c = 0; c < nch; c += S)
+                spread = std::max(spread, p->delays[(size_t)d1 * nch + c] - p->delays[(size_t)d0 * nch + c]);
+        }
+    p->sb_spread = spread;
 }
 
 // ------------------------------------------------------------- workspace
@@ -654,7 +664,9 @@ int run_subband(hp_plan* p, const Layout& L, uint8_t* ws, int32_t* out, int64_t 
             db.jobs[k] = J;
             db.prefix[k + 1] = db.prefix[k] + (int64_t)J.ntt * J.ndt;
         }
+        int ti = stage_begin(p, HP_STAGE_DEDISP, s);
         int rc = check_cuda(launch_dedisp_segmented(p->dedisp_cfg, db, p->status, p->timeout_ns, s));
+        stage_end(p, HP_STAGE_DEDISP, ti, s);
         if (rc) return rc;
         ++p->launches;
         SubbandArgs a;
@@ -665,12 +677,18 @@ int run_subband(hp_plan* p, const Layout& L, uint8_t* ws, int32_t* out, int64_t 
         a.G = p->sb_group;
         a.gchunk = T.BD;
         a.c0 = c0;
-        a.d_begin = (int32_t)std::min<int64_t>((int64_t)c0 * T.BD * p->sb_group, p->ndm());
-        a.d_end = (int32_t)std::min<int64_t>((int64_t)(c0 + n) * T.BD * p->sb_group, p->ndm());
+        a.g_begin = c0 * T.BD;
+        a.g_end = std::min((c0 + n) * T.BD, p->sb_ngrp);
+        a.ndm = p->ndm();
+        a.win_cap = (int32_t)align_up((size_t)kSubbandTile + p->sb_spread + 8, 4);
         a.out = out;
         a.out_pitch = out_pitch;
         a.nout = L.nout;
+        a.status = p->status;
+        a.timeout_ns = p->timeout_ns;
+        ti = stage_begin(p, HP_STAGE_SUBBAND_SUM, s);
         rc = check_cuda(launch_subband_sum(a, s));
+        stage_end(p, HP_STAGE_SUBBAND_SUM, ti, s);
         if (rc) return rc;
         ++p->launches;
     }
@@ -696,12 +714,7 @@ int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, const Layout& L, u
         stage_end(p, HP_STAGE_RFI, ti, s);
         if (rc) return rc;
     }
-    if (p->sb_chans > 0) {
-        ti = stage_begin(p, HP_STAGE_DEDISP, s);
-        rc = run_subband(p, L, ws, out, out_pitch, s);
-        stage_end(p, HP_STAGE_DEDISP, ti, s);
-        return rc;
-    }
+    if (p->sb_chans > 0) return run_subband(p, L, ws, out, out_pitch, s);
     DedispBatch B;   // copied into the kernel parameters at launch
     std::memset(&B, 0, sizeof(B));
     B.njobs = 1;

@@ -65,6 +65,7 @@ struct hp_plan {
     int32_t sb_nsub = 0, sb_ngrp = 0, sb_gchunk = 0, sb_nchunks = 0;
     int32_t sb_maxrel = 0;         // largest in-sub-band delay at a nominal trial
     int32_t sb_maxtop = 0;         // largest delay of a sub-band's first channel
+    int32_t sb_spread = 0;         // largest first-channel delay spread of a stage-2 block
     const int32_t* d_sbtop = nullptr;
 
     hp::DedispTiling tiling;           // for dedisp_cfg
