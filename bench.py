@@ -37,8 +37,14 @@ METRIC = "DM-trial·samples/s"
 # capture of the full-size bench command (profiles/dedisp_rows_kernel_fast_4096ch.md).
 # Keyed by the kernel source it was measured on; a changed kernel, another workload or
 # another configuration reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "2927bcfa91a72b72", "bytes": 39.94e9 + 5.74e9,
+DEDISP_TRAFFIC = {"source_sha256_16": "fb7f99522ade5692", "bytes": 37.60e9 + 5.74e9,
                   "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22}
+# The same for the two stages of the sub-band variant (64-channel sub-bands, groups
+# of 8 trials): DRAM bytes of one step (4 launches of each stage), measured per launch
+# (profiles/subband_fast_4096ch.md), keyed by both kernel sources.
+SUBBAND_TRAFFIC = {"source_sha256_16": "fb7f99522ade5692+6752b94441917dc0",
+                   "stage1": 4 * (8.64e9 + 12.80e9), "stage2": 4 * (11.75e9 + 1.45e9),
+                   "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22, "S": 64, "G": 8}
 
 
 def parse():
@@ -193,10 +199,23 @@ def measured_hbm_gbs():
         return 6800.0   # earlier GB300 measurement, used only when the file is absent
 
 
-def dedisp_traffic(w, config):
+def source_sha(name):
     import hashlib
-    src = os.path.join(ROOT, "paper_2512_00398_gb300", "csrc", "dedisp.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    src = os.path.join(ROOT, "paper_2512_00398_gb300", "csrc", name)
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def subband_traffic(w, config, S, G):
+    t = SUBBAND_TRAFFIC
+    sha = source_sha("dedisp.cu") + "+" + source_sha("subband.cu")
+    if (sha != t["source_sha256_16"] or w.ndm != t["ndm"] or w.obs.nchans != t["nchans"]
+            or w.obs.nsamps != t["nsamps"] or config != t["config"] or (S, G) != (t["S"], t["G"])):
+        return None, None
+    return t["stage1"], t["stage2"]
+
+
+def dedisp_traffic(w, config):
+    sha = source_sha("dedisp.cu")
     t = DEDISP_TRAFFIC
     if (sha != t["source_sha256_16"] or w.ndm != t["ndm"] or w.obs.nchans != t["nchans"]
             or w.obs.nsamps != t["nsamps"] or config != t["config"]):
@@ -503,6 +522,7 @@ def run_subband(args, hp, torch, stream, w, s, fb, direct_cands, peaks, hbm_peak
     bytes2 = 4.0 * nsub * ngrp * sb_len + 4.0 * w.ndm * nout
     peak_adds = 2.0 * peaks["int_add_ops_per_s"]
     t1, t2 = per["dedisp"], per["subband_sum"]
+    tr1, tr2 = subband_traffic(w, int(plan.get_param("dedisp_config")), S, G)
     plan.close()
     return {
         "what": "two-stage sub-band dedispersion (not the paper's method): identical to direct "
@@ -517,11 +537,14 @@ def run_subband(args, hp, torch, stream, w, s, fb, direct_cands, peaks, hbm_peak
         "stage1_roofline": {"bound": "alu", "kernel": "dedisp_rows_kernel (segmented)",
                             "achieved": adds1 / (t1 * 1e-3) / 1e12, "peak": peak_adds / 1e12,
                             "unit": "Tadd/s", "frac": adds1 / (t1 * 1e-3) / peak_adds,
+                            "traffic": tr1,
                             "algorithmic": f"{o.nchans} ch x {ngrp} nominal trials x {sb_len} "
                                            f"samples = {adds1:.3e} byte-adds per step"},
         "stage2_roofline": {"bound": "hbm", "kernel": "subband_sum_kernel",
                             "achieved": bytes2 / (t2 * 1e-3) / 1e9, "peak": hbm_peak,
                             "unit": "GB/s", "frac": bytes2 / (t2 * 1e-3) / 1e9 / hbm_peak,
+                            "traffic": tr2,
+                            "traffic_over_algorithmic": tr2 / bytes2 if tr2 else None,
                             "adds_tops": adds2 / (t2 * 1e-3) / 1e12,
                             "algorithmic": f"partial sums read once ({nsub} x {ngrp} x {sb_len} "
                                            f"int32) + series written ({w.ndm} x {nout} int32) "
