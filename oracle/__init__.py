@@ -59,7 +59,7 @@ class _Params(C.Structure):
                 ("widths", _P(C.c_int32)), ("nw", C.c_int), ("thr", C.c_float),
                 ("baseline_mode", C.c_int), ("baseline_s", C.c_double), ("dm_tol", C.c_int),
                 ("t_gap", C.c_int64), ("w_tol", C.c_int), ("subband_chans", C.c_int),
-                ("subband_group", C.c_int)]
+                ("subband_group", C.c_int), ("width_sigma", C.c_int)]
 
 
 def lib():
@@ -78,6 +78,7 @@ def lib():
             L.hpo_dedisperse_rows.argtypes = [vp, C.c_int64, C.c_int, vp, C.c_int, C.c_int,
                                               C.c_int64, vp]
             L.hpo_subband_delays.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+            L.hpo_width_sigma.argtypes = [vp, C.c_int64, vp, C.c_int, vp, vp]
             L.hpo_dedisperse_point.argtypes = [vp, C.c_int, vp, C.c_int64]
             L.hpo_dedisperse_point.restype = C.c_int64
             L.hpo_remedian_levels.argtypes = [C.c_int64]
@@ -213,6 +214,19 @@ def subtract_baseline(D: np.ndarray, mode: int, win: int) -> np.ndarray:
 
 
 # -------------------------------------------------------- c4 normalisation
+def width_sigma(y: np.ndarray, widths):
+    """Per-width MAD_k = lower median of |S_k(t)| over all starts and
+    sigma_k = 1.482602218505602 * MAD_k (a variant of step c4)."""
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    m = np.empty(w.size, np.int64)
+    sg = np.empty(w.size, np.float64)
+    rc = lib().hpo_width_sigma(_ptr(y), int(y.size), _ptr(w), int(w.size), _ptr(m), _ptr(sg))
+    if rc:
+        raise ValueError(f"hpo_width_sigma rc={rc}")
+    return m, sg
+
+
 def mad(y: np.ndarray) -> int:
     y = np.ascontiguousarray(y, dtype=np.int64)
     return int(lib().hpo_mad(_ptr(y), int(y.size)))
@@ -267,26 +281,28 @@ class SearchResult:
 
 
 def _params(nchans, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode, baseline_s,
-            dm_tol, t_gap, w_tol, subband=None):
+            dm_tol, t_gap, w_tol, subband=None, width_sigma=False):
     dm = np.ascontiguousarray(dm_list, dtype=np.float32)
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p = _Params(int(nchans), float(f_top), float(chan_bw), float(tsamp),
                 dm.ctypes.data_as(_P(C.c_float)), int(dm.size), w.ctypes.data_as(_P(C.c_int32)),
                 int(w.size), float(thr), int(baseline_mode), float(baseline_s), int(dm_tol),
                 int(t_gap), int(w.size if w_tol is None else w_tol),
-                int(subband[0]) if subband else 0, int(subband[1]) if subband else 1)
+                int(subband[0]) if subband else 0, int(subband[1]) if subband else 1,
+                int(bool(width_sigma)))
     return p, (dm, w)
 
 
 def search(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode=0,
            baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None, cap=1 << 22,
-           subband=None) -> SearchResult:
+           subband=None, width_sigma=False) -> SearchResult:
     """The whole hot path on a uint8[nsamps][nchans] filterbank.  subband=(S, G)
-    dedisperses with the sub-band variant's effective table (subband_delays)."""
+    dedisperses with the sub-band variant's effective table (subband_delays);
+    width_sigma=True normalises every width by its own sigma (width_sigma())."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     nsamps, nch = x.shape
     p, keep = _params(nch, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode,
-                      baseline_s, dm_tol, t_gap, w_tol, subband)
+                      baseline_s, dm_tol, t_gap, w_tol, subband, width_sigma)
     ndm = keep[0].size
     raw = np.empty(cap, dtype=RAW_DTYPE)
     cl = np.empty(cap, dtype=CLUSTER_DTYPE)
@@ -301,12 +317,12 @@ def search(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_
 
 
 def search_trials(D: np.ndarray, d_begin: int, tsamp, widths, thr, baseline_mode=0,
-                  baseline_s=2.0, cap=1 << 22):
+                  baseline_s=2.0, cap=1 << 22, width_sigma=False):
     """Per-trial stages (baseline, sigma, boxcars, peaks) on dedispersed rows."""
     D = np.ascontiguousarray(D, dtype=np.int32)
     nrows, nout = D.shape
     p, keep = _params(1, 1500.0, -1.0, tsamp, np.zeros(1, np.float32), widths, thr,
-                      baseline_mode, baseline_s, 1, 0, None)
+                      baseline_mode, baseline_s, 1, 0, None, None, width_sigma)
     raw = np.empty(cap, dtype=RAW_DTYPE)
     sig = np.empty(nrows, dtype=np.float64)
     md = np.empty(nrows, dtype=np.int64)

@@ -27,6 +27,9 @@
  *   hpo_merge             pinned: brute-force O(N^2) components, permutation invariance
  *   hpo_subband_delays    pinned: two-stage brute force, S = 1 / G = 1 / S = nchans
  *                                 reductions, closed-form error bound
+ *   hpo_width_sigma       pinned: numpy brute force, W = 1 reduction to the MAD,
+ *                                 sqrt(W) law on white noise, random-walk growth,
+ *                                 rectangular pulse S/N by hand
  */
 #include <math.h>
 #include <stdint.h>
@@ -289,6 +292,45 @@ int64_t hpo_mad(const int64_t* y, int64_t n) {
 double hpo_sigma_from_mad(int64_t mad) { return HPO_MAD_TO_SIGMA * (double)mad; }
 
 /* ------------------------------------------------------------------------
+ * Variant of step c4 that the paper does not use (per-width normalisation,
+ * as Heimdall does for its boxcar bank): every width W_k gets its own robust
+ * sigma from the boxcar series itself,
+ *   MAD_k = lower median of |S_k(t)| over the starts 0 <= t <= n - W_k,
+ *   sigma_k = 1.482602218505602 * MAD_k,
+ * with S_k(t) = sum_{i<W_k} y(t+i) as in step c5.  The threshold becomes
+ * S >= thr * sigma_k and snr = S / sigma_k (no sqrt(W) scaling); sigma_k = 0
+ * gives no candidates for that width.  On white noise sigma_k ~ sigma sqrt(W_k);
+ * on correlated (red) noise sigma_k grows faster, which lowers false
+ * detections at wide widths.  W_1 = 1 gives MAD_1 = MAD (step c4).
+ * ---------------------------------------------------------------------- */
+int hpo_width_sigma(const int64_t* y, int64_t n, const int32_t* widths, int nw,
+                    int64_t* mad_w, double* sigma_w) {
+    int64_t* a = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!a || !P) { free(a); free(P); return HPO_ERR_ARG; }
+    P[0] = 0;
+    for (int64_t i = 0; i < n; ++i) P[i + 1] = P[i] + y[i];
+    for (int k = 0; k < nw; ++k) {
+        int64_t W = widths[k];
+        int64_t m = n - W + 1;          /* number of starts */
+        int64_t mad = 0;
+        if (m > 0) {
+            for (int64_t t = 0; t < m; ++t) {
+                int64_t S = P[t + W] - P[t];
+                a[t] = S < 0 ? -S : S;
+            }
+            qsort(a, (size_t)m, sizeof(int64_t), cmp_i64);
+            mad = a[(m - 1) / 2];
+        }
+        if (mad_w) mad_w[k] = mad;
+        sigma_w[k] = HPO_MAD_TO_SIGMA * (double)mad;
+    }
+    free(a);
+    free(P);
+    return HPO_OK;
+}
+
+/* ------------------------------------------------------------------------
  * Steps c5 + c6: matched filtering by a boxcar bank and peak detection
  * (Section II-B, "Matched Filtering and Peak Detection").
  * For width W: S(t) = sum_{i=t}^{t+W-1} y(i), 0 <= t <= n - W (int64, formed
@@ -336,9 +378,13 @@ static int raw_push(raw_vec* rv, hpo_raw r) {
     return 0;
 }
 
+/* sigma_w: NULL for the paper's reading (one sigma per trial, scaled by
+ * sqrt(W)), else the per-width sigmas of hpo_width_sigma: then the limit is
+ * thr * sigma_w[k] and snr = S / sigma_w[k]. */
 static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
-                       const int32_t* widths, int nw, float thr, raw_vec* rv) {
-    if (!(sigma > 0.0)) return 0;
+                       const int32_t* widths, int nw, float thr, const double* sigma_w,
+                       raw_vec* rv) {
+    if (!sigma_w && !(sigma > 0.0)) return 0;
     int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     if (!P) return -1;
     P[0] = 0;
@@ -347,8 +393,9 @@ static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
     for (int k = 0; k < nw; ++k) {
         int64_t W = widths[k];
         if (W > n) continue;
+        if (sigma_w && !(sigma_w[k] > 0.0)) continue;
         double sw = sqrt((double)W);
-        double lim = thr_d * sigma * sw;
+        double lim = sigma_w ? thr_d * sigma_w[k] : thr_d * sigma * sw;
         int64_t last = n - W;
         int64_t t = 0;
         while (t <= last) {
@@ -367,7 +414,7 @@ static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
                 r.width_idx = k;
                 r.sample = best_t;
                 r.S = best_S;
-                r.snr = (double)best_S / (sigma * sw);
+                r.snr = sigma_w ? (double)best_S / sigma_w[k] : (double)best_S / (sigma * sw);
                 if (raw_push(rv, r)) { free(P); return -1; }
             } else {
                 ++t;
@@ -383,7 +430,7 @@ int hpo_detect_trial(const int64_t* y, int64_t n, int d, double sigma,
                      const int32_t* widths, int nw, float thr,
                      hpo_raw* out, int64_t cap, int64_t* nout) {
     raw_vec rv = {0, 0, 0};
-    if (detect_into(y, n, d, sigma, widths, nw, thr, &rv)) { free(rv.v); return HPO_ERR_ARG; }
+    if (detect_into(y, n, d, sigma, widths, nw, thr, NULL, &rv)) { free(rv.v); return HPO_ERR_ARG; }
     *nout = rv.n;
     int64_t m = rv.n < cap ? rv.n : cap;
     if (m > 0) memcpy(out, rv.v, sizeof(hpo_raw) * (size_t)m);
@@ -598,6 +645,7 @@ typedef struct {
     int w_tol;
     int subband_chans;   /* S of the sub-band variant; 0 = direct dedispersion */
     int subband_group;   /* G of the sub-band variant */
+    int width_sigma;     /* 1 = per-width sigmas (hpo_width_sigma) */
 } hpo_params;
 
 /* The delay table a search dedisperses with: step c1's, or the sub-band
@@ -648,7 +696,14 @@ int hpo_search_trials(const int32_t* D /* [nrows][nout] */, int64_t nout, int d_
         double sigma = hpo_sigma_from_mad(mad);
         if (sigma_out) sigma_out[r] = sigma;
         if (mad_out) mad_out[r] = mad;
-        if (detect_into(y, nout, d_begin + r, sigma, p->widths, p->nw, p->thr, &per[r])) bad = 1;
+        double* sw = NULL;
+        if (p->width_sigma) {
+            sw = (double*)malloc(sizeof(double) * (size_t)(p->nw > 0 ? p->nw : 1));
+            if (!sw || hpo_width_sigma(y, nout, p->widths, p->nw, NULL, sw)) bad = 1;
+        }
+        if (!bad && detect_into(y, nout, d_begin + r, sigma, p->widths, p->nw, p->thr, sw, &per[r]))
+            bad = 1;
+        free(sw);
         free(y);
     }
     int64_t tot = 0;

@@ -61,11 +61,18 @@ MUTANTS = {
     "subband_top_index": ("int top = (c / S) * S;", "int top = c / S;"),
     "subband_rel_at_trial": ("at_d[top] + at_n[c] - at_n[top]", "at_d[top] + at_d[c] - at_d[top]"),
     "subband_no_stage2_shift": ("at_d[top] + at_n[c] - at_n[top]", "at_n[c]"),
+    # per-width normalisation variant
+    "wsig_upper_median": ("mad = a[(m - 1) / 2];", "mad = a[m / 2];"),
+    "wsig_sqrt_kept": ("double lim = sigma_w ? thr_d * sigma_w[k] : thr_d * sigma * sw;",
+                       "double lim = sigma_w ? thr_d * sigma_w[k] * sw : thr_d * sigma * sw;"),
+    "wsig_starts_short": ("int64_t m = n - W + 1;", "int64_t m = n - W;"),
+    "wsig_snr_sqrt": ("r.snr = sigma_w ? (double)best_S / sigma_w[k] :",
+                      "r.snr = sigma_w ? (double)best_S / (sigma_w[k] * sw) :"),
 }
 
 # the pin files that each group of mutants is checked against
 PINS = {"rfi_": ["test_oracle_rfi.py"], "stream_": ["test_oracle_stream.py"],
-        "subband_": ["test_oracle_subband.py"]}
+        "subband_": ["test_oracle_subband.py"], "wsig_": ["test_oracle_widthsigma.py"]}
 DEFAULT_PINS = ["test_oracle_pins.py", "test_oracle_stream.py"]
 
 
