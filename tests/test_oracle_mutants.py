@@ -35,7 +35,7 @@ MUTANTS = {
     "thr_strict": ("if ((double)S >= lim) {", "if ((double)S > lim) {"),
     "peak_last_tie": ("if (S2 > best_S) { best_S = S2; best_t = t; }",
                       "if (S2 >= best_S) { best_S = S2; best_t = t; }"),
-    "snr_no_sqrt": ("r.snr = (double)best_S / (sigma * sw);", "r.snr = (double)best_S / sigma;"),
+    "snr_no_sqrt": (": (double)best_S / (sigma * sw);", ": (double)best_S / sigma;"),
     "window_short": ("int64_t S = P[t + W] - P[t];", "int64_t S = P[t + W - 1] - P[t];"),
     "merge_gap_strict": ("if (gap <= t_gap) uf_union(parent, i, j);",
                          "if (gap < t_gap) uf_union(parent, i, j);"),
