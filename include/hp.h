@@ -145,6 +145,16 @@ int hp_plan_destroy(hp_plan* plan);
  * delay of channel c per unit DM in samples. */
 #define HP_PARAM_SUBBAND_CHANS 12 /* S: channels per sub-band, 0 = direct dedispersion (default) */
 #define HP_PARAM_SUBBAND_GROUP 13 /* G: trials per group, 1..ndm (default 8) */
+/* Per-width normalisation, a variant the paper does not use (Heimdall normalises
+ * every boxcar width on its own): with HP_PARAM_WIDTH_SIGMA = 1 every width W_k
+ * gets sigma_k = 1.482602218505602 * MAD_k, MAD_k = the lower median of |S_k(t)|
+ * over every start 0 <= t <= nout - W_k (exact), the threshold is
+ * S >= thr * sigma_k (FP64), the S/N S / sigma_k, and sigma_k = 0 gives no
+ * candidates for that width.  On white noise sigma_k ~ sigma sqrt(W_k); on red
+ * noise it grows faster.  hp_search, hp_detect and batches follow it; streams
+ * refuse it.  |S_k| must stay below 2^36 (series within +-2^21 for W <= 16384),
+ * else HP_ERR_INVALID_ARG is latched.  hp_width_sigmas returns the sigmas. */
+#define HP_PARAM_WIDTH_SIGMA 14   /* 0 = one sigma per trial scaled by sqrt(W) (default), 1 = per width */
 
 #define HP_NUM_DEDISP_CONFIGS 27
 
@@ -223,6 +233,13 @@ int hp_dedisperse(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamps,
  *   mad_dev     optional device int64 [ndm]: per-trial median |y| (NULL to skip) */
 int hp_detect(hp_plan* plan, const int32_t* series_dev, int64_t nout, int64_t pitch,
               void* stream, hp_raw_buf* raw_out, double* sigma_dev, int64_t* mad_dev);
+
+/* The per-width sigmas and MADs of the last hp_search / hp_detect / batch search
+ * of this plan with HP_PARAM_WIDTH_SIGMA = 1, copied (asynchronously on `stream`)
+ * into caller-owned device arrays double [ndm][nw] / int64 [ndm][nw] (either may
+ * be NULL).  HP_ERR_INVALID_ARG when the mode is off or nothing was searched in
+ * it since it was set. */
+int hp_width_sigmas(hp_plan* plan, double* sigma_w_dev, int64_t* mad_w_dev, void* stream);
 
 /* Candidate merging and clustering (Section II-B; Algorithm 1, last stage):
  *   raw_dev / nraw_dev  device raw candidates and their device count (as

@@ -19,7 +19,7 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_PARAM_DEDISP_CONFIG, HP_PARAM_DM_TOL, HP_PARAM_RAW_CAPACITY,
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
                    HP_PARAM_RFI, HP_PARAM_RFI_NB_K, HP_PARAM_RFI_BB_K, HP_STAGE_RFI,
-                   HP_PARAM_SUBBAND_CHANS, HP_PARAM_SUBBAND_GROUP,
+                   HP_PARAM_SUBBAND_CHANS, HP_PARAM_SUBBAND_GROUP, HP_PARAM_WIDTH_SIGMA,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
                    STAGE_NAMES, HP_BATCH_MAX_FILES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks,
                    Stats, HP_STREAM_EMPTY, HP_STREAM_MAX_BEAMS, check, lib, status_str)
@@ -30,7 +30,8 @@ _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASEL
            "raw_capacity": HP_PARAM_RAW_CAPACITY, "dedisp_config": HP_PARAM_DEDISP_CONFIG,
            "stage_timing": HP_PARAM_STAGE_TIMING, "timeout_s": HP_PARAM_TIMEOUT_S,
            "rfi": HP_PARAM_RFI, "rfi_nb_k": HP_PARAM_RFI_NB_K, "rfi_bb_k": HP_PARAM_RFI_BB_K,
-           "subband_chans": HP_PARAM_SUBBAND_CHANS, "subband_group": HP_PARAM_SUBBAND_GROUP}
+           "subband_chans": HP_PARAM_SUBBAND_CHANS, "subband_group": HP_PARAM_SUBBAND_GROUP,
+           "width_sigma": HP_PARAM_WIDTH_SIGMA}
 
 
 def _torch():
@@ -289,6 +290,18 @@ def hp_rfi_clean(plan: Plan, filterbank, stream=None, cleaned: bool = True):
                              C.c_void_p(cf.data_ptr()), C.c_void_p(sf.data_ptr()),
                              C.c_void_p(med.data_ptr())), "hp_rfi_clean")
     return out, cf, sf, med
+
+
+def hp_width_sigmas(plan: Plan, stream=None):
+    """Per-width sigmas and MADs ([ndm][nw] device tensors) of the plan's last
+    search in the per-width mode."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sg = torch.empty((plan.ndm, plan.nw), dtype=torch.float64, device=dev)
+    md = torch.empty((plan.ndm, plan.nw), dtype=torch.int64, device=dev)
+    check(lib().hp_width_sigmas(plan.handle, C.c_void_p(sg.data_ptr()), C.c_void_p(md.data_ptr()),
+                                _stream_ptr(stream)), "hp_width_sigmas")
+    return sg, md
 
 
 def hp_plan_autotune(plan: Plan, filterbank, stream=None):

@@ -36,6 +36,7 @@ HP_PARAM_RFI_NB_K = 10
 HP_PARAM_RFI_BB_K = 11
 HP_PARAM_SUBBAND_CHANS = 12
 HP_PARAM_SUBBAND_GROUP = 13
+HP_PARAM_WIDTH_SIGMA = 14
 HP_NUM_DEDISP_CONFIGS = 27
 
 HP_STAGE_TRANSPOSE, HP_STAGE_DEDISP, HP_STAGE_SEARCH, HP_STAGE_MERGE, HP_STAGE_RFI = 0, 1, 2, 3, 4
@@ -59,7 +60,8 @@ EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_pa
            "hp_plan_autotune", "hp_batch_create", "hp_batch_destroy", "hp_batch_set_config",
            "hp_batch_autotune", "hp_batch_search", "hp_batch_sync_status",
            "hp_batch_kernels_per_call", "hp_stream_open", "hp_stream_push", "hp_stream_end_beam",
-           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close", "hp_plan_set_allocator", "hp_rfi_clean")
+           "hp_stream_poll", "hp_stream_get_stats", "hp_stream_close", "hp_plan_set_allocator", "hp_rfi_clean",
+           "hp_width_sigmas")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -160,6 +162,7 @@ def lib() -> C.CDLL:
             L.hp_stream_close.argtypes = [vp]
             L.hp_plan_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
             L.hp_rfi_clean.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
+            L.hp_width_sigmas.argtypes = [vp, vp, vp, vp]
             for name in EXPORTS:
                 if name != "hp_status_str":
                     getattr(L, name).restype = i32

@@ -185,6 +185,17 @@ struct TailRec {
 };
 constexpr int64_t kTailCap = 1 << 20;
 
+// Radix selection of the lower median of |S_k| for one (trial, width):
+// level 1 counts |S| >> 12 below 2^24 and |S| >> 24 above (2 x 4096 bins);
+// level 2 counts the low 12 bits of the values with
+// |S| >> 12 == prefix; level 3 the middle 12 bits of the values with
+// |S| >> 24 == prefix (then level 2 again); 0 = done.
+struct WsigState {
+    int32_t level, pad_;
+    int64_t prefix;
+    int64_t rank;              // rank of the median among the values still counted
+};
+
 struct SearchArgs {
     const int32_t* D;          // [ndm][pitch]
     int64_t pitch, nout;
@@ -229,6 +240,13 @@ struct SearchArgs {
     // 1: stop after sigma and the integer thresholds (no detection); used for the
     // zero-DM series of the RFI stage
     int stats_only;
+    // 1: per-width sigmas (sigma_k = 1.482602218505602 * lower median of |S_k|
+    // over every start) replace sigma * sqrt(W) in the thresholds and the S/N
+    int width_sigma;
+    uint32_t* whist;           // [ndm][nw][2 * 4096] radix-select counts
+    WsigState* wstate;         // [ndm][nw]
+    int64_t* wmad;             // [ndm][nw] lower median of |S_k|
+    double* sigw;              // [ndm][nw] sigma_k
 };
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch);
 
@@ -258,6 +276,7 @@ struct MergeArgs {
     const int64_t* nraw;
     int64_t cap;               // capacity of raw (== of every scratch array below)
     const double* sigma;       // [ndm]
+    const double* sigw;        // [ndm][nw] per-width sigmas, or null (sigma * sqrt(W))
     const int32_t* widths;     // device [nw]
     int nw;
     int32_t wmax;

@@ -198,6 +198,7 @@ __global__ void compress_kernel(MergeArgs a) {
 }
 
 __device__ __forceinline__ double cand_snr(const MergeArgs& a, uint64_t key, int64_t S) {
+    if (a.sigw) return __ddiv_rn((double)S, a.sigw[(int64_t)key_dm(key) * a.nw + key_width(key)]);
     const double sg = a.sigma[key_dm(key)];
     const double sw = __dsqrt_rn((double)a.widths[key_width(key)]);
     return __ddiv_rn((double)S, __dmul_rn(sg, sw));

@@ -494,6 +494,13 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
     L.mad = take((size_t)ndm * 8);
     L.sigma = take((size_t)ndm * 8);
     L.tint = take((size_t)ndm * p->nw() * 8);
+    if (p->width_sigma) {
+        const size_t pairs = (size_t)ndm * p->nw();
+        L.whist = take(pairs * 2 * 4096 * 4);
+        L.wstate = take(pairs * sizeof(WsigState));
+        L.wmad = take(pairs * 8);
+        L.sigw = take(pairs * 8);
+    }
     L.tails = take((size_t)kTailCap * sizeof(TailRec));
     L.tcount = take(8);
     const size_t cap = (size_t)p->raw_capacity;
@@ -782,6 +789,15 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.carry_out = nullptr;
     a.t_offset = 0;
     a.stats_only = 0;
+    a.width_sigma = p->width_sigma ? 1 : 0;
+    a.whist = p->width_sigma ? (uint32_t*)(ws + L.whist) : nullptr;
+    a.wstate = p->width_sigma ? (WsigState*)(ws + L.wstate) : nullptr;
+    a.wmad = p->width_sigma ? (int64_t*)(ws + L.wmad) : nullptr;
+    a.sigw = p->width_sigma ? (double*)(ws + L.sigw) : nullptr;
+    if (p->width_sigma) {
+        p->last_sigw = a.sigw;
+        p->last_wmad = a.wmad;
+    }
     return a;
 }
 
@@ -844,6 +860,7 @@ MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw
     m.nraw = nraw;
     m.cap = cap;
     m.sigma = sigma;
+    m.sigw = nullptr;   // set by the callers that searched with per-width sigmas
     m.widths = p->d_widths;
     m.nw = p->nw();
     m.wmax = p->wmax;
@@ -1004,6 +1021,7 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         rc = check_cuda(launch_search(a, si, &k));
         if (rc) return rc;
         MergeArgs m = make_merge_args(p, L, ws, raw, raw_count, p->raw_capacity, a.sigma, &outs[i]);
+        m.sigw = a.width_sigma ? a.sigw : nullptr;
         rc = check_cuda(launch_merge(m, si, &k));
         if (rc) return rc;
         rc = check_cuda(cudaEventRecord(b->done[i], si));
@@ -1040,6 +1058,7 @@ std::vector<uintptr_t> batch_key(const hp_batch* b, const uint8_t* const* fbs,
         k.push_back((uintptr_t)p->rfi);
         k.push_back((uintptr_t)p->rfi_nb_k);
         k.push_back((uintptr_t)(p->rfi_bb_k * 1e6));
+        k.push_back((uintptr_t)p->width_sigma);
     }
     return k;
 }
@@ -1169,6 +1188,12 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
             if (!(v > 0.0) || v > 1e6) return HP_ERR_INVALID_ARG;
             p->rfi_bb_k = (float)v;
             return HP_OK;
+        case HP_PARAM_WIDTH_SIGMA:
+            if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
+            p->width_sigma = v == 1.0;
+            p->last_sigw = nullptr;
+            p->last_wmad = nullptr;
+            return HP_OK;
         case HP_PARAM_SUBBAND_CHANS:
             if (v < 0 || v > p->nchans || v != std::floor(v)) return HP_ERR_INVALID_ARG;
             p->sb_chans = (int)v;
@@ -1200,6 +1225,7 @@ int hp_plan_get_param(const hp_plan* p, int param, double* v) {
         case HP_PARAM_RFI_NB_K: *v = p->rfi_nb_k; return HP_OK;
         case HP_PARAM_RFI_BB_K: *v = (double)p->rfi_bb_k; return HP_OK;
         case HP_PARAM_SUBBAND_CHANS: *v = p->sb_chans; return HP_OK;
+        case HP_PARAM_WIDTH_SIGMA: *v = p->width_sigma ? 1.0 : 0.0; return HP_OK;
         case HP_PARAM_SUBBAND_GROUP: *v = p->sb_group; return HP_OK;
         default: return HP_ERR_INVALID_ARG;
     }
@@ -1370,9 +1396,25 @@ int hp_search(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream, hp_ca
     stage_end(p, HP_STAGE_SEARCH, ti, s);
     if (rc) return rc;
     MergeArgs m = make_merge_args(p, L, ws, raw, raw_count, p->raw_capacity, a.sigma, out);
+    m.sigw = a.width_sigma ? a.sigw : nullptr;
     ti = stage_begin(p, HP_STAGE_MERGE, s);
     rc = check_cuda(launch_merge(m, s, &p->launches));
     stage_end(p, HP_STAGE_MERGE, ti, s);
+    return rc;
+}
+
+int hp_width_sigmas(hp_plan* p, double* sigma_w_dev, int64_t* mad_w_dev, void* stream) {
+    if (!p || (!sigma_w_dev && !mad_w_dev)) return HP_ERR_INVALID_ARG;
+    if (!p->width_sigma || !p->last_sigw) return HP_ERR_INVALID_ARG;
+    const size_t pairs = (size_t)p->ndm() * p->nw();
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = HP_OK;
+    if (sigma_w_dev)
+        rc = check_cuda(cudaMemcpyAsync(sigma_w_dev, p->last_sigw, pairs * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+    if (!rc && mad_w_dev)
+        rc = check_cuda(cudaMemcpyAsync(mad_w_dev, p->last_wmad, pairs * sizeof(int64_t),
+                                        cudaMemcpyDeviceToDevice, s));
     return rc;
 }
 

@@ -28,6 +28,7 @@ struct Layout {
            r_lvl_a = 0, r_lvl_b = 0, r_mean = 0, r_zhist = 0, r_bucket = 0, r_rank = 0,
            r_mad = 0, r_sigma = 0, r_tint = 0, r_y = 0;
     int64_t r_zpitch = 0, r_lvl_pitch_a = 0, r_lvl_pitch_b = 0, r_mean_pitch = 0;
+    size_t whist = 0, wstate = 0, wmad = 0, sigw = 0;   // per-width sigmas (if enabled)
     size_t sb = 0;             // sub-band partial sums (sub-band variant)
     int64_t sb_pitch = 0, sb_len = 0;
     int sb_chunks = 0;         // DM-tile chunks whose partial sums fit `sb` at once
@@ -84,6 +85,9 @@ struct hp_plan {
     int32_t* d_widths = nullptr;
 
     // device allocator for the plan's tables and workspace (default cudaMalloc)
+    bool width_sigma = false;      // per-width sigmas instead of sigma * sqrt(W)
+    const double* last_sigw = nullptr;   // where the last search put them ([ndm][nw])
+    const int64_t* last_wmad = nullptr;
     bool rfi = false;              // RFI mitigation before dedispersion
     int rfi_nb_k = 5;
     float rfi_bb_k = 5.0f;

@@ -676,6 +676,159 @@ __global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// ------------------------------------------------- per-width sigmas
+// The lower median of |S_k(t)| over the starts 0 <= t <= n - W_k of every
+// (trial, width), exact, by radix selection over 12-bit digits (WsigState):
+// each histogram pass rebuilds the boxcar sums of a 4096-start tile from an
+// int64 prefix of y in shared memory and counts the digit of every value
+// still in the running, per width into one shared histogram.
+constexpr int kWsigTile = 4096;
+constexpr int kWsigBins = 2 * 4096;   // level 1: v >> 12 below 2^24 | v >> 24
+
+__device__ __forceinline__ int wsig_bin(int level, int64_t v, int64_t prefix) {
+    if (level == 1)
+        return v < ((int64_t)1 << 24) ? (int)(v >> 12) : 4096 + (int)min(v >> 24, (int64_t)4095);
+    if (level == 2) return (v >> 12) == prefix ? (int)(v & 4095) : -1;
+    return (v >> 24) == prefix ? (int)((v >> 12) & 4095) : -1;
+}
+
+__global__ void wsig_init_kernel(const __grid_constant__ SearchArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)a.ndm * a.nw) return;
+    const int64_t m = a.nout - a.widths[i % a.nw] + 1;     // starts
+    WsigState st;
+    st.level = m > 0 ? 1 : 0;
+    st.pad_ = 0;
+    st.prefix = 0;
+    st.rank = m > 0 ? (m - 1) / 2 : 0;
+    a.wstate[i] = st;
+    if (m <= 0) a.wmad[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) wsig_hist_kernel(const __grid_constant__ SearchArgs a,
+                                                        int level) {
+    extern __shared__ int64_t P[];   // P[i] = sum of y over samples [t0, t0 + i)
+    __shared__ uint32_t h[kWsigBins];
+    __shared__ int64_t warp_tot[32];
+    const int trial = blockIdx.y;
+    const WsigState* st = a.wstate + (int64_t)trial * a.nw;
+    bool any = false;
+    for (int k = 0; k < a.nw; ++k) any = any || st[k].level == level;
+    if (!any) return;                                     // the whole block
+    const int64_t n = a.nout;
+    const int64_t t0 = (int64_t)blockIdx.x * kWsigTile;
+    const int64_t len = min((int64_t)kWsigTile + a.wmax - 1, n - t0);
+    const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
+    const int tid = threadIdx.x;
+    for (int64_t i = tid; i < len; i += blockDim.x) P[i + 1] = (int64_t)yrow[t0 + i];
+    __syncthreads();
+    const int64_t per = ((len + blockDim.x - 1) / blockDim.x) | 1;
+    const int64_t i0 = min(len, tid * per), i1 = min(len, i0 + per);
+    int64_t local = 0;
+    for (int64_t i = i0; i < i1; ++i) local += P[i + 1];
+    int64_t run = block_exclusive_scan(local, warp_tot);  // (synchronises)
+    for (int64_t i = i0; i < i1; ++i) {
+        run += P[i + 1];
+        P[i + 1] = run;
+    }
+    if (tid == 0) P[0] = 0;
+    __syncthreads();
+    const int bins = level == 1 ? kWsigBins : 4096;
+    for (int i = tid; i < bins; i += blockDim.x) h[i] = 0;
+    for (int k = 0; k < a.nw; ++k) {
+        const WsigState sk = st[k];
+        if (sk.level != level) continue;                  // uniform over the block
+        __syncthreads();
+        const int64_t W = a.widths[k];
+        const int64_t t_end = min(t0 + kWsigTile, n - W + 1);   // starts of this tile
+        bool big = false;
+        for (int64_t t = t0 + tid; t < t_end; t += blockDim.x) {
+            const int64_t S = P[t - t0 + W] - P[t - t0];
+            const int64_t v = S < 0 ? -S : S;
+            big = big || v >= ((int64_t)1 << 36);
+            const int b = wsig_bin(level, v, sk.prefix);
+            if (b >= 0) atomicAdd(&h[b], 1u);
+        }
+        if (big) latch_status(a.status, HP_ERR_INVALID_ARG);   // |S| beyond the digits counted
+        __syncthreads();
+        // flush the counts and clear them for the next width
+        uint32_t* g = a.whist + ((int64_t)trial * a.nw + k) * kWsigBins;
+        for (int i = tid; i < bins; i += blockDim.x) {
+            const uint32_t c = h[i];
+            if (c) {
+                atomicAdd(&g[i], c);
+                h[i] = 0;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) wsig_select_kernel(const __grid_constant__ SearchArgs a,
+                                                           int level) {
+    const int64_t idx = blockIdx.x;                       // trial * nw + k
+    WsigState st = a.wstate[idx];
+    if (st.level != level) return;                        // the whole block
+    uint32_t* hrow = a.whist + idx * kWsigBins;
+    int bin;
+    int64_t before;
+    find_rank_bin(hrow, level == 1 ? kWsigBins : 4096, st.rank, &bin, &before);
+    if (threadIdx.x == 0) {
+        if (level == 1) {
+            st.level = bin < 4096 ? 2 : 3;
+            st.prefix = bin < 4096 ? bin : bin - 4096;
+            st.rank -= before;
+        } else if (level == 2) {
+            a.wmad[idx] = (st.prefix << 12) + bin;
+            st.level = 0;
+        } else {
+            st.level = 2;
+            st.prefix = (st.prefix << 12) | bin;
+            st.rank -= before;
+        }
+        a.wstate[idx] = st;
+    }
+    __syncthreads();
+    if (st.level != 0)   // the next level counts into the first 4096 bins
+        for (int i = threadIdx.x; i < 4096; i += blockDim.x) hrow[i] = 0;
+}
+
+// sigma_k and the integer thresholds ceil(thr * sigma_k)
+__global__ void wsig_sigma_kernel(const __grid_constant__ SearchArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)a.ndm * a.nw) return;
+    const double sg = __dmul_rn(kMadToSigma, (double)a.wmad[i]);
+    a.sigw[i] = sg;
+    a.tint[i] = sg > 0.0 ? (int64_t)ceil(__dmul_rn((double)a.thr, sg)) : kNever;
+}
+
+cudaError_t launch_width_sigma(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch) {
+    cudaError_t e;
+    const int64_t pairs = (int64_t)a.ndm * a.nw;
+    if ((e = cudaMemsetAsync(a.whist, 0, (size_t)pairs * kWsigBins * 4, s)) != cudaSuccess) return e;
+    ++*nlaunch;
+    wsig_init_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = ((size_t)kWsigTile + (size_t)a.wmax + 1) * sizeof(int64_t);
+    if ((e = cudaFuncSetAttribute(wsig_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const dim3 hgrid((unsigned)ceil_div(a.nout, kWsigTile), a.ndm);
+    // levels 1, 2 and the rare 3 -> 2 path for medians of 2^24 or more
+    const int order[] = {1, 2, 3, 2};
+    for (int level : order) {
+        ++*nlaunch;
+        wsig_hist_kernel<<<hgrid, 256, smem, s>>>(a, level);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*nlaunch;
+        wsig_select_kernel<<<(unsigned)pairs, 1024, 0, s>>>(a, level);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    ++*nlaunch;
+    wsig_sigma_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+
 template <int MODE>
 cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStream_t s,
                            int64_t* nlaunch) {
@@ -703,6 +856,7 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
                                                               a.sigma, a.tint);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.stats_only) return cudaSuccess;
+    if (a.width_sigma && (e = launch_width_sigma(a, s, nlaunch)) != cudaSuccess) return e;
     const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
     if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)

@@ -209,3 +209,27 @@ def test_subband_params_and_workspace():
         nb = p.nout(1 << 20) + int(p.delays()[:, ::64].max())
         assert ws - direct_ws >= 2 * 64 * 24 * nb * 4
         assert ws < direct_ws + (16 << 30) + (1 << 30)
+
+
+def test_width_sigma_param_and_arguments():
+    import ctypes as C
+    w = workloads.tiny()
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold) as p:
+        assert p.get_param("width_sigma") == 0
+        for bad in (2, -1, 0.5):
+            with pytest.raises(hp.HPError):
+                p.set_param("width_sigma", bad)
+        L = hp.lib()
+        buf = C.create_string_buffer(8)
+        # mode off, or on with nothing searched yet: refused before any CUDA call
+        assert L.hp_width_sigmas(p.handle, buf, None, None) == hp.HP_ERR_INVALID_ARG
+        p.set_param("width_sigma", 1)
+        assert p.get_param("width_sigma") == 1
+        assert L.hp_width_sigmas(p.handle, buf, None, None) == hp.HP_ERR_INVALID_ARG
+        assert L.hp_width_sigmas(p.handle, None, None, None) == hp.HP_ERR_INVALID_ARG
+        assert L.hp_width_sigmas(None, buf, None, None) == hp.HP_ERR_INVALID_ARG
+        ws_on = p.workspace_bytes(o.nsamps)
+        p.set_param("width_sigma", 0)
+        # the radix-select counts: [ndm][nw][2 x 4096] uint32
+        assert ws_on - p.workspace_bytes(o.nsamps) >= w.ndm * len(w.widths) * 2 * 4096 * 4
