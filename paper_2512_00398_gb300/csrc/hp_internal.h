@@ -185,13 +185,11 @@ struct TailRec {
 };
 constexpr int64_t kTailCap = 1 << 20;
 
-// Radix selection of the lower median of |S_k| for one (trial, width):
-// level 1 counts |S| >> 12 below 2^24 and |S| >> 24 above (2 x 4096 bins);
-// level 2 counts the low 12 bits of the values with
-// |S| >> 12 == prefix; level 3 the middle 12 bits of the values with
-// |S| >> 24 == prefix (then level 2 again); 0 = done.
+// Radix selection of the lower median of |S_k| for one (trial, width): pass
+// `level` (0 = done) counts, among the values with v >> shift == prefix, the
+// next digit (the first pass: v >> shift, plus an overflow range).
 struct WsigState {
-    int32_t level, pad_;
+    int32_t level, shift;
     int64_t prefix;
     int64_t rank;              // rank of the median among the values still counted
 };
@@ -243,7 +241,7 @@ struct SearchArgs {
     // 1: per-width sigmas (sigma_k = 1.482602218505602 * lower median of |S_k|
     // over every start) replace sigma * sqrt(W) in the thresholds and the S/N
     int width_sigma;
-    uint32_t* whist;           // [ndm][nw][2 * 4096] radix-select counts
+    uint32_t* whist;           // [ndm][nw][2 * 4096] radix-selection counts
     WsigState* wstate;         // [ndm][nw]
     int64_t* wmad;             // [ndm][nw] lower median of |S_k|
     double* sigw;              // [ndm][nw] sigma_k

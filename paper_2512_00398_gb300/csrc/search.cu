@@ -678,27 +678,43 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------- per-width sigmas
 // The lower median of |S_k(t)| over the starts 0 <= t <= n - W_k of every
-// (trial, width), exact, by radix selection over 12-bit digits (WsigState):
-// each histogram pass rebuilds the boxcar sums of a 4096-start tile from an
-// int64 prefix of y in shared memory and counts the digit of every value
-// still in the running, per width into one shared histogram.
+// (trial, width), exact, by radix selection (WsigState).  Each histogram
+// pass rebuilds the boxcar sums of a 4096-start tile from a prefix of y in
+// shared memory and counts one digit of every value still in the running,
+// per width into one shared histogram.  The first pass counts v >> s0 below
+// 4096 (and v >> (s0 + 12) above, up to 4095), with s0 chosen from the
+// trial's MAD and sqrt(W) so that the values spread over ~1000 bins (few
+// same-bin atomics) and narrow widths finish in that pass; later passes count
+// the next (up to) 12 bits below the digits fixed so far.  A median in the
+// last first-pass bin (values beyond what that pass resolves) restarts from
+// the top digit of the 36-bit range.
 constexpr int kWsigTile = 4096;
-constexpr int kWsigBins = 2 * 4096;   // level 1: v >> 12 below 2^24 | v >> 24
+constexpr int kWsigBins = 2 * 4096;
+constexpr int kWsigTop = 36;          // |S| < 2^36 (checked)
+constexpr int kWsigPasses = 4;        // first pass + at most three 12-bit digits
 
-__device__ __forceinline__ int wsig_bin(int level, int64_t v, int64_t prefix) {
-    if (level == 1)
-        return v < ((int64_t)1 << 24) ? (int)(v >> 12) : 4096 + (int)min(v >> 24, (int64_t)4095);
-    if (level == 2) return (v >> 12) == prefix ? (int)(v & 4095) : -1;
-    return (v >> 24) == prefix ? (int)((v >> 12) & 4095) : -1;
+__device__ __forceinline__ int wsig_bin(const WsigState& st, uint64_t v) {
+    if (st.level == 1) {
+        const uint64_t key = v >> st.shift;
+        return key < 4096 ? (int)key : 4096 + (int)min(v >> (st.shift + 12), (uint64_t)4095);
+    }
+    if ((int64_t)(v >> st.shift) != st.prefix) return -1;
+    const int d = min(12, st.shift);
+    return (int)((v >> (st.shift - d)) & ((1u << d) - 1u));
 }
 
 __global__ void wsig_init_kernel(const __grid_constant__ SearchArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)a.ndm * a.nw) return;
-    const int64_t m = a.nout - a.widths[i % a.nw] + 1;     // starts
+    const int32_t W = a.widths[i % a.nw];
+    const int64_t m = a.nout - W + 1;                     // starts
+    // first-pass shift: log2 of the expected median, MAD * sqrt(W), less 9
+    const int64_t mad = a.mad[i / a.nw];
+    const int lm = 63 - __clzll((unsigned long long)max(mad, (int64_t)1));
+    const int lw = (31 - __clz(W)) / 2;
     WsigState st;
     st.level = m > 0 ? 1 : 0;
-    st.pad_ = 0;
+    st.shift = min(max(lm + lw - 9, 0), kWsigTop - 12);
     st.prefix = 0;
     st.rank = m > 0 ? (m - 1) / 2 : 0;
     a.wstate[i] = st;
@@ -710,6 +726,8 @@ __global__ void __launch_bounds__(256) wsig_hist_kernel(const __grid_constant__ 
     extern __shared__ int64_t P[];   // P[i] = sum of y over samples [t0, t0 + i)
     __shared__ uint32_t h[kWsigBins];
     __shared__ int64_t warp_tot[32];
+    __shared__ int64_t warp_max[32];
+    __shared__ int bin_lo, bin_hi;
     const int trial = blockIdx.y;
     const WsigState* st = a.wstate + (int64_t)trial * a.nw;
     bool any = false;
@@ -717,43 +735,115 @@ __global__ void __launch_bounds__(256) wsig_hist_kernel(const __grid_constant__ 
     if (!any) return;                                     // the whole block
     const int64_t n = a.nout;
     const int64_t t0 = (int64_t)blockIdx.x * kWsigTile;
-    const int64_t len = min((int64_t)kWsigTile + a.wmax - 1, n - t0);
-    const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
-    const int tid = threadIdx.x;
-    for (int64_t i = tid; i < len; i += blockDim.x) P[i + 1] = (int64_t)yrow[t0 + i];
+    const int len = (int)min((int64_t)kWsigTile + a.wmax - 1, n - t0);
+    const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch + t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < len; i += blockDim.x) P[i + 1] = (int64_t)yrow[i];
     __syncthreads();
-    const int64_t per = ((len + blockDim.x - 1) / blockDim.x) | 1;
-    const int64_t i0 = min(len, tid * per), i1 = min(len, i0 + per);
-    int64_t local = 0;
-    for (int64_t i = i0; i < i1; ++i) local += P[i + 1];
+    const int per = ((len + (int)blockDim.x - 1) / (int)blockDim.x) | 1;
+    const int i0 = min(len, tid * per), i1 = min(len, i0 + per);
+    int64_t local = 0, ymax = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int64_t y = P[i + 1];
+        local += y;
+        ymax = max(ymax, y < 0 ? -y : y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ymax = max(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    if (lane == 0) warp_max[warp] = ymax;
     int64_t run = block_exclusive_scan(local, warp_tot);  // (synchronises)
-    for (int64_t i = i0; i < i1; ++i) {
+    for (int i = i0; i < i1; ++i) {
         run += P[i + 1];
         P[i + 1] = run;
     }
-    if (tid == 0) P[0] = 0;
+    if (tid == 0) {
+        P[0] = 0;
+        bin_lo = kWsigBins;
+        bin_hi = -1;
+    }
     __syncthreads();
-    const int bins = level == 1 ? kWsigBins : 4096;
-    for (int i = tid; i < bins; i += blockDim.x) h[i] = 0;
+    int64_t tile_max = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tile_max = max(tile_max, warp_max[w]);
+    // every boxcar sum of this tile fits int32: wrapped 32-bit differences of
+    // the prefix's low words are exact
+    const bool narrow = tile_max * (int64_t)a.wmax < (int64_t)INT32_MAX;
+    const uint32_t* P32 = reinterpret_cast<const uint32_t*>(P);   // low word of P[i]: P32[2 i]
+    for (int i = tid; i < kWsigBins; i += blockDim.x) h[i] = 0;
     for (int k = 0; k < a.nw; ++k) {
         const WsigState sk = st[k];
         if (sk.level != level) continue;                  // uniform over the block
         __syncthreads();
-        const int64_t W = a.widths[k];
-        const int64_t t_end = min(t0 + kWsigTile, n - W + 1);   // starts of this tile
+        const int W = a.widths[k];
+        const int t_end = (int)min((int64_t)kWsigTile, n - W + 1 - t0);   // starts of this tile
+        int lo = kWsigBins, hi = -1;
         bool big = false;
-        for (int64_t t = t0 + tid; t < t_end; t += blockDim.x) {
-            const int64_t S = P[t - t0 + W] - P[t - t0];
-            const int64_t v = S < 0 ? -S : S;
-            big = big || v >= ((int64_t)1 << 36);
-            const int b = wsig_bin(level, v, sk.prefix);
-            if (b >= 0) atomicAdd(&h[b], 1u);
+        if (narrow) {
+            // every |S| < 2^31: the digit in 32-bit arithmetic (a shift of 31
+            // or more leaves 0)
+            const int sh = sk.shift;
+            const uint32_t s1 = (uint32_t)min(sh, 31), s2 = (uint32_t)min(sh + 12, 31);
+            const bool z1 = sh >= 31, z2 = sh + 12 >= 31;
+            const int d = min(12, sh);
+            const uint32_t s3 = (uint32_t)min(sh - d, 31);
+            const bool z3 = sh - d >= 31;
+            const uint32_t mask = (1u << d) - 1u;
+            const bool reach = sk.prefix < ((int64_t)1 << 31);   // a 31-bit value can match
+            const uint32_t pre = (uint32_t)sk.prefix;
+            if (level == 1) {
+                for (int t = tid; t < t_end; t += blockDim.x) {
+                    const int32_t S = (int32_t)(P32[2 * (t + W)] - P32[2 * t]);
+                    const uint32_t v = S < 0 ? 0u - (uint32_t)S : (uint32_t)S;
+                    const uint32_t k1 = z1 ? 0u : v >> s1;
+                    const int b = k1 < 4096u ? (int)k1 : 4096 + (int)min(z2 ? 0u : v >> s2, 4095u);
+                    atomicAdd(&h[b], 1u);
+                    lo = min(lo, b);
+                    hi = max(hi, b);
+                }
+            } else if (reach) {
+                for (int t = tid; t < t_end; t += blockDim.x) {
+                    const int32_t S = (int32_t)(P32[2 * (t + W)] - P32[2 * t]);
+                    const uint32_t v = S < 0 ? 0u - (uint32_t)S : (uint32_t)S;
+                    if ((z1 ? 0u : v >> s1) == pre) {
+                        const int b = (int)((z3 ? 0u : v >> s3) & mask);
+                        atomicAdd(&h[b], 1u);
+                        lo = min(lo, b);
+                        hi = max(hi, b);
+                    }
+                }
+            }
+        } else {
+            for (int t = tid; t < t_end; t += blockDim.x) {
+                const int64_t S = P[t + W] - P[t];
+                const uint64_t v = S < 0 ? (uint64_t)(-S) : (uint64_t)S;
+                big = big || v >= ((uint64_t)1 << kWsigTop);
+                const int b = wsig_bin(sk, v);
+                if (b >= 0) {
+                    atomicAdd(&h[b], 1u);
+                    lo = min(lo, b);
+                    hi = max(hi, b);
+                }
+            }
         }
-        if (big) latch_status(a.status, HP_ERR_INVALID_ARG);   // |S| beyond the digits counted
+        if (big) latch_status(a.status, HP_ERR_INVALID_ARG);   // |S| beyond the 36-bit range
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0 && hi >= 0) {
+            atomicMin(&bin_lo, lo);
+            atomicMax(&bin_hi, hi);
+        }
         __syncthreads();
-        // flush the counts and clear them for the next width
+        const int b0 = bin_lo, b1 = bin_hi;
+        __syncthreads();                                  // every thread has read the range
+        if (tid == 0) {
+            bin_lo = kWsigBins;
+            bin_hi = -1;
+        }
+        // flush the touched bins and clear them for the next width
         uint32_t* g = a.whist + ((int64_t)trial * a.nw + k) * kWsigBins;
-        for (int i = tid; i < bins; i += blockDim.x) {
+        for (int i = b0 + tid; i <= b1; i += blockDim.x) {
             const uint32_t c = h[i];
             if (c) {
                 atomicAdd(&g[i], c);
@@ -769,26 +859,34 @@ __global__ void __launch_bounds__(1024) wsig_select_kernel(const __grid_constant
     WsigState st = a.wstate[idx];
     if (st.level != level) return;                        // the whole block
     uint32_t* hrow = a.whist + idx * kWsigBins;
+    const int nbins = level == 1 ? kWsigBins : 1 << min(12, st.shift);
     int bin;
     int64_t before;
-    find_rank_bin(hrow, level == 1 ? kWsigBins : 4096, st.rank, &bin, &before);
+    find_rank_bin(hrow, nbins, st.rank, &bin, &before);
     if (threadIdx.x == 0) {
-        if (level == 1) {
-            st.level = bin < 4096 ? 2 : 3;
+        if (level == 1 && bin == kWsigBins - 1) {
+            // beyond what the first pass resolves: every digit from the top
+            st.prefix = 0;
+            st.shift = kWsigTop;
+        } else if (level == 1) {
             st.prefix = bin < 4096 ? bin : bin - 4096;
+            st.shift = bin < 4096 ? st.shift : st.shift + 12;
             st.rank -= before;
-        } else if (level == 2) {
-            a.wmad[idx] = (st.prefix << 12) + bin;
-            st.level = 0;
         } else {
-            st.level = 2;
-            st.prefix = (st.prefix << 12) | bin;
+            const int d = min(12, st.shift);
+            st.prefix = (st.prefix << d) | bin;
+            st.shift -= d;
             st.rank -= before;
+        }
+        st.level = level + 1;
+        if (st.shift == 0) {
+            a.wmad[idx] = st.prefix;
+            st.level = 0;
         }
         a.wstate[idx] = st;
     }
     __syncthreads();
-    if (st.level != 0)   // the next level counts into the first 4096 bins
+    if (a.wstate[idx].level != 0)   // the next pass counts into the first bins
         for (int i = threadIdx.x; i < 4096; i += blockDim.x) hrow[i] = 0;
 }
 
@@ -813,9 +911,7 @@ cudaError_t launch_width_sigma(const SearchArgs& a, cudaStream_t s, int64_t* nla
                                   (int)smem)) != cudaSuccess)
         return e;
     const dim3 hgrid((unsigned)ceil_div(a.nout, kWsigTile), a.ndm);
-    // levels 1, 2 and the rare 3 -> 2 path for medians of 2^24 or more
-    const int order[] = {1, 2, 3, 2};
-    for (int level : order) {
+    for (int level = 1; level <= kWsigPasses; ++level) {
         ++*nlaunch;
         wsig_hist_kernel<<<hgrid, 256, smem, s>>>(a, level);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

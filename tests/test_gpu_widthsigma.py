@@ -3,8 +3,8 @@
 The per-width MADs must equal the oracle's exactly (the radix selection is
 exact), the sigmas bit for bit (the same FP64 product), the raw candidates'
 tuples and sums exactly and the S/N within 1e-4; the whole search must give
-the oracle's clusters.  Magnitudes beyond 2^24 take the selection's third
-level and are checked too.
+the oracle's clusters.  Large magnitudes and a median beyond the first pass (the
+restart from the top digit) are checked too.
 """
 import numpy as np
 import pytest
@@ -80,7 +80,7 @@ def test_detect_sigmas_and_raw_exact(hp, torch, tiny):
         assert np.array_equal(sg[d], s_o), d
 
 
-def test_large_magnitudes_take_the_third_level(hp, torch):
+def test_large_magnitudes(hp, torch):
     """Series of +-2^20: the medians of |S_k| for the wide widths lie above
     2^24, where the selection counts the high digits first."""
     from paper_2512_00398_gb300 import synth
@@ -101,6 +101,30 @@ def test_large_magnitudes_take_the_third_level(hp, torch):
         m_o, s_o = oracle.width_sigma(y, widths)
         assert np.array_equal(md[d], m_o), d
         assert np.array_equal(sg[d], s_o), d
+    assert _key(raw_g) == _key(raw_o)
+
+
+def test_median_beyond_the_first_pass(hp, torch):
+    """A series whose MAD is 0 (three samples in five are 0) while most wide
+    boxcars sum to more than 2^24: the first pass, sized from the MAD, cannot
+    resolve the median and the selection restarts from the top digit."""
+    nout = 30000
+    t = np.arange(nout)
+    D = np.where(t % 5 < 2, 1 << 20, 0).astype(np.int32)[None, :].repeat(2, axis=0)
+    D[1, ::7] += 3
+    widths = np.array([1, 8, 64, 1024], np.int32)
+    p = hp.Plan(64, 1500.0, -1.0, 1e-3, np.zeros(2, np.float32), widths, 6.0, width_sigma=1)
+    raw_g, _, mad_g = hp.detect(p, torch.from_numpy(D).cuda(), nout)
+    assert hp.hp_plan_sync_status(p) == hp.HP_OK
+    sg, md = (t_.cpu().numpy() for t_ in hp.hp_width_sigmas(p))
+    win = oracle.baseline_window(2.0, 1e-3)
+    raw_o, _, _ = oracle.search_trials(D, 0, 1e-3, widths, 6.0, width_sigma=True)
+    for d in range(2):
+        y = oracle.subtract_baseline(D[d], 0, win)
+        m_o, s_o = oracle.width_sigma(y, widths)
+        assert np.array_equal(md[d], m_o), (d, md[d], m_o)
+        assert np.array_equal(sg[d], s_o), d
+    assert mad_g[0] == 0 and md[0, 2] > (1 << 24)
     assert _key(raw_g) == _key(raw_o)
 
 
