@@ -147,3 +147,24 @@ def test_subband_fast_full_size_sampled(hp, torch):
     for d in (0, 383, w.ndm - 1):
         Do = oracle.dedisperse(s.data, eff, rows=(d, d + 1))
         assert np.array_equal(Do[0], D[d, :nout].cpu().numpy()), d
+
+
+def test_subband_search_with_rfi_matches_oracle(hp, torch, tiny):
+    """RFI mitigation before the two stages: the oracle cleans the input, then
+    searches it with the effective table."""
+    w, s, fb, tab = tiny
+    o = w.obs
+    x = s.data.astype(np.int32)
+    x[:, [5, 77]] += 45
+    x[::2999, :] += 40
+    x = np.clip(x, 0, 255).astype(np.uint8)
+    clean = oracle.rfi_clean(x, o.tsamp).cleaned
+    want = oracle.search(clean, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                         subband=(16, 4))
+    p = _plan(hp, w, subband_chans=16, subband_group=4, rfi=1)
+    got = hp.search(p, torch.from_numpy(x).cuda())
+    key = lambda c: (int(c["dm_idx"]), int(c["sample"]), int(c["width_idx"]))
+    assert len(want.clusters) > 0
+    assert [key(c) for c in got] == [key(c) for c in want.clusters]
+    for a, b in zip(got, want.clusters):
+        assert abs(float(a["snr"]) - float(b["snr"])) <= SNR_TOL
