@@ -679,7 +679,8 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // ------------------------------------------------- per-width sigmas
 // The lower median of |S_k(t)| over the starts 0 <= t <= n - W_k of every
 // (trial, width), exact, by radix selection (WsigState).  Each histogram
-// pass rebuilds the boxcar sums of a 4096-start tile from a prefix of y in
+// pass rebuilds the boxcar sums of a tile of up to 16384 starts (one block of
+// 1024 threads) from a prefix of y over the tile and its halo in
 // shared memory and counts one digit of every value still in the running,
 // per width into one shared histogram.  The first pass counts v >> s0 below
 // 4096 (and v >> (s0 + 12) above, up to 4095), with s0 chosen from the
@@ -688,7 +689,8 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // the next (up to) 12 bits below the digits fixed so far.  A median in the
 // last first-pass bin (values beyond what that pass resolves) restarts from
 // the top digit of the 36-bit range.
-constexpr int kWsigTile = 4096;
+constexpr int kWsigThreads = 1024;
+constexpr int kWsigTileMax = 16384;   // starts per block (fewer when the halo is wide)
 constexpr int kWsigBins = 2 * 4096;
 constexpr int kWsigTop = 36;          // |S| < 2^36 (checked)
 constexpr int kWsigPasses = 4;        // first pass + at most three 12-bit digits
@@ -721,8 +723,8 @@ __global__ void wsig_init_kernel(const __grid_constant__ SearchArgs a) {
     if (m <= 0) a.wmad[i] = 0;
 }
 
-__global__ void __launch_bounds__(256) wsig_hist_kernel(const __grid_constant__ SearchArgs a,
-                                                        int level) {
+__global__ void __launch_bounds__(kWsigThreads) wsig_hist_kernel(const __grid_constant__ SearchArgs a,
+                                                                 int level, int tile) {
     extern __shared__ int64_t P[];   // P[i] = sum of y over samples [t0, t0 + i)
     __shared__ uint32_t h[kWsigBins];
     __shared__ int64_t warp_tot[32];
@@ -734,8 +736,8 @@ __global__ void __launch_bounds__(256) wsig_hist_kernel(const __grid_constant__ 
     for (int k = 0; k < a.nw; ++k) any = any || st[k].level == level;
     if (!any) return;                                     // the whole block
     const int64_t n = a.nout;
-    const int64_t t0 = (int64_t)blockIdx.x * kWsigTile;
-    const int len = (int)min((int64_t)kWsigTile + a.wmax - 1, n - t0);
+    const int64_t t0 = (int64_t)blockIdx.x * tile;
+    const int len = (int)min((int64_t)tile + a.wmax - 1, n - t0);
     const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch + t0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < len; i += blockDim.x) P[i + 1] = (int64_t)yrow[i];
@@ -774,7 +776,7 @@ __global__ void __launch_bounds__(256) wsig_hist_kernel(const __grid_constant__ 
         if (sk.level != level) continue;                  // uniform over the block
         __syncthreads();
         const int W = a.widths[k];
-        const int t_end = (int)min((int64_t)kWsigTile, n - W + 1 - t0);   // starts of this tile
+        const int t_end = (int)min((int64_t)tile, n - W + 1 - t0);   // starts of this tile
         int lo = kWsigBins, hi = -1;
         bool big = false;
         if (narrow) {
@@ -906,14 +908,17 @@ cudaError_t launch_width_sigma(const SearchArgs& a, cudaStream_t s, int64_t* nla
     ++*nlaunch;
     wsig_init_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t smem = ((size_t)kWsigTile + (size_t)a.wmax + 1) * sizeof(int64_t);
+    // the widest tile whose prefix (tile + halo) fits beside the static arrays
+    int tile = kWsigTileMax;
+    while (tile > 1024 && ((size_t)tile + a.wmax + 1) * sizeof(int64_t) > (size_t)190 * 1024) tile /= 2;
+    const size_t smem = ((size_t)tile + (size_t)a.wmax + 1) * sizeof(int64_t);
     if ((e = cudaFuncSetAttribute(wsig_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
-    const dim3 hgrid((unsigned)ceil_div(a.nout, kWsigTile), a.ndm);
+    const dim3 hgrid((unsigned)ceil_div(a.nout, tile), a.ndm);
     for (int level = 1; level <= kWsigPasses; ++level) {
         ++*nlaunch;
-        wsig_hist_kernel<<<hgrid, 256, smem, s>>>(a, level);
+        wsig_hist_kernel<<<hgrid, kWsigThreads, smem, s>>>(a, level, tile);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++*nlaunch;
         wsig_select_kernel<<<(unsigned)pairs, 1024, 0, s>>>(a, level);
