@@ -151,8 +151,8 @@ int hp_plan_destroy(hp_plan* plan);
  * over every start 0 <= t <= nout - W_k (exact), the threshold is
  * S >= thr * sigma_k (FP64), the S/N S / sigma_k, and sigma_k = 0 gives no
  * candidates for that width.  On white noise sigma_k ~ sigma sqrt(W_k); on red
- * noise it grows faster.  hp_search, hp_detect and batches follow it; streams
- * refuse it.  |S_k| must stay below 2^36 (series within +-2^21 for W <= 16384),
+ * noise it grows faster.  hp_search, hp_detect, batches and streams follow it
+ * (a stream's sigmas are those of each searched buffer).  |S_k| must stay below 2^36 (series within +-2^21 for W <= 16384),
  * else HP_ERR_INVALID_ARG is latched.  hp_width_sigmas returns the sigmas. */
 #define HP_PARAM_WIDTH_SIGMA 14   /* 0 = one sigma per trial scaled by sqrt(W) (default), 1 = per width */
 

@@ -458,9 +458,9 @@ int hpo_detect_trial(const int64_t* y, int64_t n, int d, double sigma,
 static int detect_window_into(const int64_t* y, int64_t n, int d, double sigma,
                               const int32_t* widths, int nw, float thr, int64_t nwin,
                               const uint8_t* carry_in, uint8_t* carry_out, int64_t t_offset,
-                              raw_vec* rv) {
+                              const double* sigma_w, raw_vec* rv) {
     for (int k = 0; k < nw; ++k) carry_out[k] = 0;
-    if (!(sigma > 0.0)) return 0;
+    if (!sigma_w && !(sigma > 0.0)) return 0;
     int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     if (!P) return -1;
     P[0] = 0;
@@ -468,7 +468,8 @@ static int detect_window_into(const int64_t* y, int64_t n, int d, double sigma,
     for (int k = 0; k < nw; ++k) {
         int64_t W = widths[k];
         if (W > n) continue;
-        double lim = (double)thr * sigma * sqrt((double)W);
+        if (sigma_w && !(sigma_w[k] > 0.0)) continue;
+        double lim = sigma_w ? (double)thr * sigma_w[k] : (double)thr * sigma * sqrt((double)W);
         int64_t last = n - W;
         if (nwin >= 1 && nwin - 1 <= last)
             carry_out[k] = (double)(P[nwin - 1 + W] - P[nwin - 1]) >= lim;
@@ -489,7 +490,7 @@ static int detect_window_into(const int64_t* y, int64_t n, int d, double sigma,
             r.width_idx = k;
             r.sample = best_t + t_offset;
             r.S = best_S;
-            r.snr = (double)best_S / (sigma * sqrt((double)W));
+            r.snr = sigma_w ? (double)best_S / sigma_w[k] : (double)best_S / (sigma * sqrt((double)W));
             if (raw_push(rv, r)) { free(P); return -1; }
         }
     }
@@ -502,7 +503,7 @@ int hpo_detect_window(const int64_t* y, int64_t n, int d, double sigma, const in
                       uint8_t* carry_out, int64_t t_offset, hpo_raw* out, int64_t cap,
                       int64_t* nout) {
     raw_vec rv = {0, 0, 0};
-    if (detect_window_into(y, n, d, sigma, widths, nw, thr, nwin, carry_in, carry_out, t_offset,
+    if (detect_window_into(y, n, d, sigma, widths, nw, thr, nwin, carry_in, carry_out, t_offset, NULL,
                            &rv)) {
         free(rv.v);
         return HPO_ERR_ARG;
@@ -786,10 +787,16 @@ int hpo_search_window(const uint8_t* x, int64_t nsamps, const hpo_params* p, int
         if (!y) { bad = 1; continue; }
         if (hpo_subtract_baseline(D + (int64_t)d * nout, nout, p->baseline_mode, win, y)) bad = 1;
         double sigma = hpo_sigma_from_mad(hpo_mad(y, nout));
-        if (detect_window_into(y, nout, d, sigma, p->widths, p->nw, p->thr, nwin,
-                               carry_in ? carry_in + (int64_t)d * p->nw : NULL,
-                               carry_out + (int64_t)d * p->nw, t_offset, &per[d]))
+        double* sw = NULL;
+        if (p->width_sigma) {
+            sw = (double*)malloc(sizeof(double) * (size_t)(p->nw > 0 ? p->nw : 1));
+            if (!sw || hpo_width_sigma(y, nout, p->widths, p->nw, NULL, sw)) bad = 1;
+        }
+        if (!bad && detect_window_into(y, nout, d, sigma, p->widths, p->nw, p->thr, nwin,
+                                       carry_in ? carry_in + (int64_t)d * p->nw : NULL,
+                                       carry_out + (int64_t)d * p->nw, t_offset, sw, &per[d]))
             bad = 1;
+        free(sw);
         free(y);
     }
     free(D);

@@ -332,6 +332,7 @@ int enqueue_step(hp_stream* s, Step* st) {
             out.capacity = s->cfg.cand_capacity;
             out.count = s->dcount[j];
             MergeArgs mg = make_merge_args(p, L, ws, raw, raw_count, p->raw_capacity, a.sigma, &out);
+            mg.sigw = a.width_sigma ? a.sigw : nullptr;
             rc = check_cuda(launch_merge(mg, sj, &kernels));
             if (rc) return rc;
             rc = check_cuda(cudaMemcpyAsync(item_count(s, st->set, j), s->dcount[j], sizeof(int64_t),
@@ -402,6 +403,7 @@ int copy_plan(const hp_plan* t, int64_t raw_capacity, hp_plan** out) {
     p->rfi = t->rfi;
     p->rfi_nb_k = t->rfi_nb_k;
     p->rfi_bb_k = t->rfi_bb_k;
+    p->width_sigma = t->width_sigma;
     return HP_OK;
 }
 
@@ -430,7 +432,6 @@ int hp_stream_open(hp_stream** out, const hp_plan* tmpl, const hp_stream_config*
     *out = nullptr;
     if (!tmpl || !cfg) return HP_ERR_INVALID_ARG;
     if (tmpl->sb_chans > 0) return HP_ERR_INVALID_ARG;   // direct dedispersion only
-    if (tmpl->width_sigma) return HP_ERR_INVALID_ARG;    // one sigma per trial only
     if (cfg->nbeams < 1 || cfg->nbeams > HP_STREAM_MAX_BEAMS) return HP_ERR_INVALID_ARG;
     if (cfg->max_batch < 0 || cfg->max_batch > HP_BATCH_MAX_FILES) return HP_ERR_INVALID_ARG;
     if (cfg->gulp < 64 || cfg->gulp >= kMaxSamples / 4) return HP_ERR_INVALID_ARG;

@@ -139,7 +139,7 @@ def test_batch_matches_per_file(hp, torch, tiny):
     b.close()
 
 
-def test_mode_switch_and_refusals(hp, torch, tiny):
+def test_mode_switch(hp, torch, tiny):
     w, s, fb = tiny
     p = _plan(hp, w)
     with pytest.raises(hp.HPError):
@@ -153,8 +153,45 @@ def test_mode_switch_and_refusals(hp, torch, tiny):
     assert sg.shape == (w.ndm, len(w.widths))
     p.set_param("width_sigma", 0)
     assert np.array_equal(hp.search(p, fb), plain)
-    with pytest.raises(hp.HPError):
-        hp.Stream(_plan(hp, w, width_sigma=1), nbeams=1, gulp=4096)
+
+
+def test_stream_matches_oracle(hp, torch):
+    """Two beams pushed gulp by gulp in the per-width mode: every gulp's
+    clusters equal the oracle's streamed search with the sigmas of each
+    searched buffer."""
+    from paper_2512_00398_gb300 import workloads
+    G = 4096
+    ws = workloads.stream_tiny(nbeams=2, ngulps=6, gulp=G)
+    data = [w_.generate().data for w_ in ws]
+    w = ws[0]
+    o = w.obs
+    st = hp.Stream(_plan(hp, w, width_sigma=1), nbeams=2, gulp=G)
+    for g in range(6):
+        for b in range(2):
+            st.push(b, data[b][g * G:(g + 1) * G])
+    for b in range(2):
+        st.end_beam(b)
+    got = {}
+    while len(got) < 12:
+        r = st.poll(timeout_ms=120000)
+        assert r is not None, "stream stalled"
+        info, c = r
+        assert info["status"] == hp.HP_OK
+        got[(info["beam"], info["gulp_index"])] = c
+    st.close()
+    n = 0
+    for b in range(2):
+        want = oracle.stream_search(data[b], G, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths,
+                                    w.threshold, width_sigma=True)
+        for r in want:
+            c, wc = got[(b, r["g"])], r["clusters"]
+            assert len(c) == len(wc)
+            for f in ("dm_idx", "width_idx", "sample", "members", "dm_lo", "dm_hi", "t_lo", "t_hi"):
+                assert np.array_equal(c[f], wc[f]), f
+            if len(c):
+                assert np.abs(c["snr"].astype(np.float64) - wc["snr"]).max() <= SNR_TOL
+            n += len(wc)
+    assert n > 0
 
 
 def test_fast_full_size_sampled(hp, torch):

@@ -67,7 +67,7 @@ MUTANTS = {
                        "double lim = sigma_w ? thr_d * sigma_w[k] * sw : thr_d * sigma * sw;"),
     "wsig_starts_short": ("int64_t m = n - W + 1;", "int64_t m = n - W;"),
     "wsig_snr_sqrt": ("r.snr = sigma_w ? (double)best_S / sigma_w[k] :",
-                      "r.snr = sigma_w ? (double)best_S / (sigma_w[k] * sw) :"),
+                      "r.snr = sigma_w ? (double)best_S / (sigma_w[k] * sqrt((double)widths[k])) :"),
 }
 
 # the pin files that each group of mutants is checked against

@@ -118,3 +118,45 @@ def test_search_mode_off_is_the_paper_reading(tiny_workload):
                       width_sigma=True)
     for p in s.pulses:
         assert workloads.recovered(p, c.clusters, w), p
+
+
+def test_stream_window_with_width_sigma(tiny_workload):
+    """One gulp's buffer in the per-width mode: runs of S_k >= thr * sigma_k with
+    sigma_k from the buffer, kept when their first start lies in the window;
+    carry flags = start nwin - 1 above threshold."""
+    w, s = tiny_workload
+    o = w.obs
+    tab = oracle.delays(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list)
+    maxd, wmax = int(tab.max()), int(w.widths.max())
+    N = 3 * 4096
+    x = s.data[:N]
+    nwin = N - maxd - wmax + 1
+    raw, cl, cout = oracle.search_window(x, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths,
+                                         w.threshold, nwin, 0, width_sigma=True)
+    D = oracle.dedisperse(x, tab)
+    win = oracle.baseline_window(2.0, o.tsamp)
+    thr = float(np.float32(w.threshold))
+    want = []
+    for d in range(D.shape[0]):
+        y = oracle.subtract_baseline(D[d], 0, win)
+        c = np.concatenate([[0], np.cumsum(y)])
+        for k, W in enumerate(w.widths):
+            S = c[W:] - c[:-W]
+            sk = 1.482602218505602 * float(_brute_mad(y, int(W)))
+            above = S.astype(np.float64) >= thr * sk if sk > 0 else np.zeros(S.size, bool)
+            assert cout[d, k] == int(above[nwin - 1])
+            t = 0
+            while t < S.size:
+                if not above[t]:
+                    t += 1
+                    continue
+                e = t
+                while e < S.size and above[e]:
+                    e += 1
+                if t < nwin:
+                    j = t + int(np.argmax(S[t:e]))
+                    want.append((d, k, j, int(S[j])))
+                t = e
+    got = sorted((int(z["dm_idx"]), int(z["width_idx"]), int(z["sample"]), int(z["S"]))
+                 for z in raw)
+    assert got == sorted(want) and len(got) > 0
