@@ -139,9 +139,10 @@ int hp_plan_destroy(hp_plan* plan);
  * This equals direct dedispersion with the effective table
  * e(c,d) = delay(top(s),d) + delay(c,n(g(d))) - delay(top(s),n(g(d))), which
  * hp_plan_delays then returns (hp_plan_max_delay its maximum; nout = nsamps -
- * that maximum).  hp_search, hp_dedisperse and hp_plan_autotune follow the
- * variant (byte-row tile shapes only); batches and streams refuse it
- * (HP_ERR_INVALID_ARG).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
+ * that maximum).  hp_search, hp_dedisperse, hp_plan_autotune, batches (the
+ * variant's files through their own two stages; hp_batch_autotune refuses it)
+ * and streams (per searched buffer) follow the variant (tile shapes 17, 21,
+ * 22 and 24 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
  * delay of channel c per unit DM in samples. */
 #define HP_PARAM_SUBBAND_CHANS 12 /* S: channels per sub-band, 0 = direct dedispersion (default) */
 #define HP_PARAM_SUBBAND_GROUP 13 /* G: trials per group, 1..ndm (default 8) */

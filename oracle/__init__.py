@@ -356,13 +356,14 @@ def detect_window(y: np.ndarray, d: int, sigma: float, widths, thr: float, nwin:
 
 def search_window(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, nwin: int,
                   t_offset: int, carry_in=None, baseline_mode=0, baseline_s=2.0, dm_tol=1,
-                  t_gap=0, w_tol=None, cap=1 << 22, width_sigma=False):
+                  t_gap=0, w_tol=None, cap=1 << 22, width_sigma=False, subband=None):
     """One gulp's buffer searched with the window rule; returns (raw, clusters,
-    carry_out[ndm][nw]).  width_sigma=True: per-width sigmas of the buffer."""
+    carry_out[ndm][nw]).  width_sigma=True: per-width sigmas of the buffer;
+    subband=(S, G): the sub-band variant's effective table."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     nsamps, nch = x.shape
     p, keep = _params(nch, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode,
-                      baseline_s, dm_tol, t_gap, w_tol, None, width_sigma)
+                      baseline_s, dm_tol, t_gap, w_tol, subband, width_sigma)
     ndm, nw = keep[0].size, keep[1].size
     cin = None if carry_in is None else np.ascontiguousarray(carry_in, dtype=np.uint8)
     cout = np.zeros((ndm, nw), dtype=np.uint8)
@@ -389,15 +390,19 @@ def gulp_geometry(g: int, gulp: int, maxd: int, wmax: int):
 
 def stream_search(x: np.ndarray, gulp: int, f_top, chan_bw, tsamp, dm_list, widths, thr,
                   baseline_mode=0, baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None, rfi=None,
-                  width_sigma=False):
+                  width_sigma=False, subband=None):
     """A beam's whole series x[nsamps][nchans] searched gulp by gulp; the last
     partial gulp is dropped.  Returns one dict per gulp: g, B0, nwin, raw,
     clusters (samples in the beam's dedispersed time).  rfi=(nb_k, bb_k) cleans
     each searched buffer first (its own statistics, step c0); width_sigma=True
-    normalises every width by its own sigma over the searched buffer."""
+    normalises every width by its own sigma over the searched buffer;
+    subband=(S, G) dedisperses with the sub-band variant (the gulp geometry then
+    follows its effective table)."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     nch = x.shape[1]
     tab = delays(nch, f_top, chan_bw, tsamp, dm_list)
+    if subband:
+        tab = subband_delays(tab, subband[0], subband[1])
     maxd = int(tab.max())
     wmax = int(np.max(widths))
     out, carry = [], None
@@ -412,7 +417,7 @@ def stream_search(x: np.ndarray, gulp: int, f_top, chan_bw, tsamp, dm_list, widt
             buf = rfi_clean(buf, tsamp, rfi[0], rfi[1], baseline_mode, baseline_s).cleaned
         raw, cl, carry = search_window(buf, f_top, chan_bw, tsamp, dm_list, widths, thr,
                                        nwin, B0, carry, baseline_mode, baseline_s, dm_tol, t_gap,
-                                       w_tol, width_sigma=width_sigma)
+                                       w_tol, width_sigma=width_sigma, subband=subband)
         out.append({"g": g, "B0": B0, "nwin": nwin, "raw": raw, "clusters": cl})
     return out
 

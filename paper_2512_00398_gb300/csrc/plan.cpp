@@ -956,7 +956,6 @@ int batch_prepare(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         hp_plan* p = b->plans[i];
         int rc = validate_search_input(p, fbs ? fbs[i] : nullptr, nsamps[i]);
         if (rc) return rc;
-        if (p->sb_chans > 0) return HP_ERR_INVALID_ARG;   // direct dedispersion only
         p->dedisp_cfg = b->cfg;
         rc = ensure_device_tables(p);
         if (rc) return rc;
@@ -977,17 +976,21 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
     std::memset(&tb, 0, sizeof(tb));
     DedispBatch db;
     std::memset(&db, 0, sizeof(db));
-    tb.njobs = db.njobs = n;
+    tb.njobs = n;
+    int nd = 0;   // files dedispersed directly, in the one batched launch
     for (int i = 0; i < n; ++i) {
         hp_plan* p = b->plans[i];
         const Layout& L = Ls[i];
         tb.jobs[i] = make_transpose_job(fbs[i], nsamps[i], p->nchans, wss[i] + L.xt, L.xt_pitch);
         tb.prefix[i + 1] = tb.prefix[i] + tb.jobs[i].ttiles * tb.jobs[i].ctiles;
+        if (p->sb_chans > 0) continue;      // the sub-band variant runs its own two stages
         if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
-        db.jobs[i] = make_job(p, wss[i] + L.xt, L.xt_pitch, (int32_t*)(wss[i] + L.D), L.dpitch,
-                              L.nout);
-        db.prefix[i + 1] = db.prefix[i] + (int64_t)db.jobs[i].ntt * db.jobs[i].ndt;
+        db.jobs[nd] = make_job(p, wss[i] + L.xt, L.xt_pitch, (int32_t*)(wss[i] + L.D), L.dpitch,
+                               L.nout);
+        db.prefix[nd + 1] = db.prefix[nd] + (int64_t)db.jobs[nd].ntt * db.jobs[nd].ndt;
+        ++nd;
     }
+    db.njobs = nd;
     int64_t k = 0;
     int rc = check_cuda(launch_transpose_batch(tb, s));
     if (rc) return rc;
@@ -1002,9 +1005,20 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         if (rc) return rc;
     }
     hp_plan* p0 = b->plans[0];
-    rc = check_cuda(launch_dedisp(b->cfg, db, p0->status, p0->timeout_ns, s));
-    if (rc) return rc;
-    ++k;
+    if (nd > 0) {
+        rc = check_cuda(launch_dedisp(b->cfg, db, p0->status, p0->timeout_ns, s));
+        if (rc) return rc;
+        ++k;
+    }
+    for (int i = 0; i < n; ++i) {
+        hp_plan* p = b->plans[i];
+        if (p->sb_chans <= 0) continue;
+        const Layout& L = Ls[i];
+        const int64_t before = p->launches;
+        rc = run_subband(p, L, wss[i], (int32_t*)(wss[i] + L.D), L.dpitch, s);
+        if (rc) return rc;
+        k += p->launches - before;
+    }
     rc = check_cuda(cudaEventRecord(b->fork, s));
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
@@ -1059,6 +1073,8 @@ std::vector<uintptr_t> batch_key(const hp_batch* b, const uint8_t* const* fbs,
         k.push_back((uintptr_t)p->rfi_nb_k);
         k.push_back((uintptr_t)(p->rfi_bb_k * 1e6));
         k.push_back((uintptr_t)p->width_sigma);
+        k.push_back((uintptr_t)p->sb_chans);
+        k.push_back((uintptr_t)p->sb_group);
     }
     return k;
 }
@@ -1554,6 +1570,8 @@ int hp_batch_search(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamp
 int hp_batch_autotune(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps, void* stream,
                       int* best_config, float* best_ms) {
     if (!b || !fbs || !nsamps) return HP_ERR_INVALID_ARG;
+    for (hp_plan* p : b->plans)
+        if (p->sb_chans > 0) return HP_ERR_INVALID_ARG;   // direct dedispersion only
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)b->plans.size();
     const int keep = b->cfg;

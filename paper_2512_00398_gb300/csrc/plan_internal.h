@@ -124,6 +124,9 @@ int validate_search_input(const hp_plan* p, const void* ptr, int64_t nsamps);
 bool reach_ok(const hp_plan* p, int64_t nout, int64_t xt_pitch);
 DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_t* out,
                    int64_t out_pitch, int64_t nout);
+// Stages 1 and 2 of the sub-band variant on the transposed input at ws + L.xt.
+int run_subband(hp_plan* p, const Layout& L, uint8_t* ws, int32_t* out, int64_t out_pitch,
+                cudaStream_t s);
 SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int32_t* D,
                             int64_t pitch, int64_t nout, hp_raw_cand* raw, int64_t raw_cap,
                             int64_t* raw_count);

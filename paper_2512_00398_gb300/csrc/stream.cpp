@@ -290,14 +290,17 @@ int enqueue_step(hp_stream* s, Step* st) {
         J.ring_slots = s->R;
         tb.jobs[j] = J;
         tb.prefix[j + 1] = tb.prefix[j] + J.ttiles * J.ctiles;
-        if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
-        db.jobs[j] = make_job(p, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, L.nout);
-        db.prefix[j + 1] = db.prefix[j] + (int64_t)db.jobs[j].ntt * db.jobs[j].ndt;
+        if (p->sb_chans <= 0) {   // the sub-band variant runs its own two stages per gulp
+            if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
+            db.jobs[j] = make_job(p, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, L.nout);
+            db.prefix[j + 1] = db.prefix[j] + (int64_t)db.jobs[j].ntt * db.jobs[j].ndt;
+        }
         work.push_back(&it);
     }
     const int n = (int)work.size();
     if (n > 0) {
-        tb.njobs = db.njobs = n;
+        tb.njobs = n;
+        db.njobs = p->sb_chans > 0 ? 0 : n;
         rc = check_cuda(launch_transpose_batch(tb, m));
         int64_t rfi_kernels = 0;
         for (int j = 0; j < n && !rc && p->rfi; ++j) {   // RFI mitigation per searched buffer
@@ -305,7 +308,10 @@ int enqueue_step(hp_stream* s, Step* st) {
                                             Ls[j].xt_pitch, work[j]->E - work[j]->B0, nullptr);
             rc = check_cuda(launch_rfi(r, m, &rfi_kernels));
         }
-        if (!rc) rc = check_cuda(launch_dedisp(p->dedisp_cfg, db, p->status, p->timeout_ns, m));
+        if (!rc && db.njobs > 0)
+            rc = check_cuda(launch_dedisp(p->dedisp_cfg, db, p->status, p->timeout_ns, m));
+        for (int j = 0; j < n && !rc && p->sb_chans > 0; ++j)
+            rc = run_subband(p, Ls[j], s->ws[j], (int32_t*)(s->ws[j] + Ls[j].D), Ls[j].dpitch, m);
         if (!rc) rc = check_cuda(cudaEventRecord(s->fork, m));
         if (rc) return rc;
         int64_t kernels = 0;
@@ -404,6 +410,15 @@ int copy_plan(const hp_plan* t, int64_t raw_capacity, hp_plan** out) {
     p->rfi_nb_k = t->rfi_nb_k;
     p->rfi_bb_k = t->rfi_bb_k;
     p->width_sigma = t->width_sigma;
+    if (t->sb_chans > 0) {
+        rc = hp_plan_set_param(p, HP_PARAM_SUBBAND_GROUP, t->sb_group);
+        if (!rc) rc = hp_plan_set_param(p, HP_PARAM_SUBBAND_CHANS, t->sb_chans);
+        if (rc) {
+            hp_plan_destroy(p);
+            *out = nullptr;
+            return rc;
+        }
+    }
     return HP_OK;
 }
 
@@ -431,7 +446,6 @@ int hp_stream_open(hp_stream** out, const hp_plan* tmpl, const hp_stream_config*
     if (!out) return HP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!tmpl || !cfg) return HP_ERR_INVALID_ARG;
-    if (tmpl->sb_chans > 0) return HP_ERR_INVALID_ARG;   // direct dedispersion only
     if (cfg->nbeams < 1 || cfg->nbeams > HP_STREAM_MAX_BEAMS) return HP_ERR_INVALID_ARG;
     if (cfg->max_batch < 0 || cfg->max_batch > HP_BATCH_MAX_FILES) return HP_ERR_INVALID_ARG;
     if (cfg->gulp < 64 || cfg->gulp >= kMaxSamples / 4) return HP_ERR_INVALID_ARG;

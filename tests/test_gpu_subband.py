@@ -108,18 +108,64 @@ def test_subband_autotune_and_direct_switch(hp, torch, tiny):
     assert np.array_equal(hp.dedisperse(p, fb), oracle.dedisperse(s.data, tab))
 
 
-def test_subband_refused_by_batch_and_stream(hp, torch, tiny):
+def test_subband_in_a_batch_matches_per_file(hp, torch, tiny):
+    """A batch mixing a sub-band file and a direct file: the direct file in the
+    batched launch, the sub-band file through its own two stages; each equal to
+    its plain search (eager, captured, replayed); batch autotuning refuses it."""
     w, s, fb, tab = tiny
-    p = _plan(hp, w, subband_chans=16)
+    p_sb, p_d = _plan(hp, w, subband_chans=16, subband_group=4), _plan(hp, w)
+    want = [hp.search(_plan(hp, w, subband_chans=16, subband_group=4), fb), hp.search(_plan(hp, w), fb)]
+    b = hp.Batch([p_sb, p_d])
+    for _ in range(3):
+        got = b.search([fb, fb])
+        for g, w_ in zip(got, want):
+            assert np.array_equal(g, w_)
     with pytest.raises(hp.HPError):
-        hp.Stream(p, nbeams=1, gulp=4096)
-    b = hp.Batch([p])
-    with pytest.raises(hp.HPError):
-        b.search([fb])
+        b.autotune([fb, fb])
     b.close()
     # a tile shape without the segmented stage 1
     with pytest.raises(hp.HPError):
         hp.dedisperse(_plan(hp, w, dedisp_config=0, subband_chans=16), fb)
+
+
+def test_subband_stream_matches_oracle(hp, torch):
+    """Two beams streamed with the sub-band variant: every gulp's clusters equal
+    the oracle's streamed search on the effective table."""
+    from paper_2512_00398_gb300 import workloads
+    G = 4096
+    ws = workloads.stream_tiny(nbeams=2, ngulps=6, gulp=G)
+    data = [w_.generate().data for w_ in ws]
+    w = ws[0]
+    o = w.obs
+    st = hp.Stream(_plan(hp, w, subband_chans=16, subband_group=4), nbeams=2, gulp=G)
+    for g in range(6):
+        for b in range(2):
+            st.push(b, data[b][g * G:(g + 1) * G])
+    for b in range(2):
+        st.end_beam(b)
+    got = {}
+    while len(got) < 12:
+        r = st.poll(timeout_ms=120000)
+        assert r is not None, "stream stalled"
+        info, c = r
+        assert info["status"] == hp.HP_OK
+        got[(info["beam"], info["gulp_index"])] = (info, c)
+    st.close()
+    n = 0
+    for b in range(2):
+        want = oracle.stream_search(data[b], G, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths,
+                                    w.threshold, subband=(16, 4))
+        for r in want:
+            info, c = got[(b, r["g"])]
+            assert info["window_start"] == r["B0"] and info["window_len"] == r["nwin"]
+            wc = r["clusters"]
+            assert len(c) == len(wc)
+            for f in ("dm_idx", "width_idx", "sample", "members", "dm_lo", "dm_hi", "t_lo", "t_hi"):
+                assert np.array_equal(c[f], wc[f]), f
+            if len(c):
+                assert np.abs(c["snr"].astype(np.float64) - wc["snr"]).max() <= SNR_TOL
+            n += len(wc)
+    assert n > 0
 
 
 def test_subband_fast_full_size_sampled(hp, torch):

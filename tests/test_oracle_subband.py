@@ -132,3 +132,20 @@ def test_argument_errors():
         oracle.subband_delays(d, 0, 2)
     with pytest.raises(ValueError):
         oracle.subband_delays(d, 2, 0)
+
+
+def test_stream_reduces_to_direct_at_one_channel_per_subband():
+    """The streamed search takes the variant's table and geometry: with one
+    channel per sub-band it is the direct streamed search, gulp by gulp."""
+    from paper_2512_00398_gb300 import workloads
+    ws = workloads.stream_tiny(nbeams=1, ngulps=5, gulp=4096)
+    w = ws[0]
+    x = w.generate().data
+    o = w.obs
+    a = oracle.stream_search(x, 4096, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    b = oracle.stream_search(x, 4096, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                             subband=(1, 3))
+    assert [r["B0"] for r in a] == [r["B0"] for r in b]
+    for ra, rb in zip(a, b):
+        assert np.array_equal(ra["clusters"], rb["clusters"])
+    assert sum(len(r["clusters"]) for r in a) > 0
