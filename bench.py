@@ -425,6 +425,17 @@ def run_ours(args):
                           f"{peaks['sm_count']} SMs",
             "frac_vs_int32_rate": achieved / peaks["int_add_ops_per_s"],
         }
+        # shared-memory loads: NW + 1 row words per lane, channel and trial for NW
+        # words of 4 samples (byte-row kernels), against the measured LDS.32 rate
+        shape = hp.hp_dedisp_config(cfg)
+        if shape["layout"] == 2:
+            lds_bytes = adds * (shape["NW"] + 1) / shape["NW"]
+            line["roofline"]["lds"] = {
+                "achieved_tbs": lds_bytes / (dd_ms * 1e-3) / 1e12,
+                "peak_tbs": peaks["lds32_bytes_per_s"] / 1e12,
+                "frac": lds_bytes / (dd_ms * 1e-3) / peaks["lds32_bytes_per_s"],
+                "basis": f"{shape['NW'] + 1} LDS.32 per {shape['NW']} words of 4 samples per "
+                         "(trial, channel); measured conflict-free LDS.32 rate"}
         # the per-trial stages: the histogram pass reads D and writes y, the
         # detect pass reads y (the remedian reads D once more at 1/5 of the
         # rate it walks); per (trial, sample) nw threshold tests + 1 prefix add

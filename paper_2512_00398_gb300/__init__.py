@@ -488,6 +488,14 @@ def hp_plan_stats(plan: Plan, reset: bool = True) -> dict:
             "kernel_launches": int(st.kernel_launches)}
 
 
+def hp_dedisp_config(config: int) -> dict:
+    """The shape of a dedispersion tile shape (no GPU needed)."""
+    out = (C.c_int32 * 8)()
+    check(lib().hp_dedisp_config(int(config), out), "hp_dedisp_config")
+    keys = ("RD", "NW", "WD", "WT", "stage_bytes", "producers", "layout", "stages")
+    return dict(zip(keys, (int(v) for v in out)))
+
+
 def hp_measure_peaks() -> dict:
     """Integer-add, byte-permute and shared-memory load rates of the current GPU."""
     pk = Peaks()

@@ -4,6 +4,7 @@
 // rates are the best of three event-timed launches after a warm-up.
 #include "../../include/hp_bench.h"
 #include "common.cuh"
+#include "hp_internal.h"
 
 namespace hp {
 namespace {
@@ -99,6 +100,14 @@ double best_ms(K kernel, int blocks, uint32_t* out) {
 
 }  // namespace
 }  // namespace hp
+
+extern "C" int hp_dedisp_config(int config, int32_t out[8]) {
+    if (!out || config < 0 || config >= hp::kNumDedispConfigs) return HP_ERR_INVALID_ARG;
+    const hp::DedispConfig& c = hp::kDedispConfigs[config];
+    const int32_t v[8] = {c.RD, c.NW, c.WD, c.WT, c.stage_bytes, c.producers, c.layout, c.stages};
+    for (int i = 0; i < 8; ++i) out[i] = v[i];
+    return HP_OK;
+}
 
 extern "C" int hp_measure_peaks(hp_peaks* out) {
     using namespace hp;

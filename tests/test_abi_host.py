@@ -233,3 +233,15 @@ def test_width_sigma_param_and_arguments():
         p.set_param("width_sigma", 0)
         # the radix-select counts: [ndm][nw][2 x 4096] uint32
         assert ws_on - p.workspace_bytes(o.nsamps) >= w.ndm * len(w.widths) * 2 * 4096 * 4
+
+
+def test_dedisp_config_shapes():
+    shapes = [hp.hp_dedisp_config(c) for c in range(hp.HP_NUM_DEDISP_CONFIGS)]
+    assert shapes[22] == {"RD": 2, "NW": 7, "WD": 12, "WT": 1, "stage_bytes": 54 * 1024,
+                          "producers": 1, "layout": 2, "stages": 4}
+    assert all(s["layout"] in (0, 1, 2) and s["RD"] >= 1 and s["NW"] >= 1 for s in shapes)
+    # byte-row kernels keep an odd word count per lane (conflict-free row loads)
+    assert all(s["NW"] % 2 == 1 for s in shapes if s["layout"] == 2)
+    for bad in (-1, hp.HP_NUM_DEDISP_CONFIGS):
+        with pytest.raises(hp.HPError):
+            hp.hp_dedisp_config(bad)
