@@ -59,7 +59,7 @@ class _Params(C.Structure):
                 ("widths", _P(C.c_int32)), ("nw", C.c_int), ("thr", C.c_float),
                 ("baseline_mode", C.c_int), ("baseline_s", C.c_double), ("dm_tol", C.c_int),
                 ("t_gap", C.c_int64), ("w_tol", C.c_int), ("subband_chans", C.c_int),
-                ("subband_group", C.c_int), ("width_sigma", C.c_int)]
+                ("subband_group", C.c_int), ("width_sigma", C.c_int), ("decimate", C.c_int)]
 
 
 def lib():
@@ -281,7 +281,7 @@ class SearchResult:
 
 
 def _params(nchans, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode, baseline_s,
-            dm_tol, t_gap, w_tol, subband=None, width_sigma=False):
+            dm_tol, t_gap, w_tol, subband=None, width_sigma=False, decimate=0):
     dm = np.ascontiguousarray(dm_list, dtype=np.float32)
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p = _Params(int(nchans), float(f_top), float(chan_bw), float(tsamp),
@@ -289,20 +289,22 @@ def _params(nchans, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode, 
                 int(w.size), float(thr), int(baseline_mode), float(baseline_s), int(dm_tol),
                 int(t_gap), int(w.size if w_tol is None else w_tol),
                 int(subband[0]) if subband else 0, int(subband[1]) if subband else 1,
-                int(bool(width_sigma)))
+                int(bool(width_sigma)), int(decimate))
     return p, (dm, w)
 
 
 def search(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode=0,
            baseline_s=2.0, dm_tol=1, t_gap=0, w_tol=None, cap=1 << 22,
-           subband=None, width_sigma=False) -> SearchResult:
+           subband=None, width_sigma=False, decimate=0) -> SearchResult:
     """The whole hot path on a uint8[nsamps][nchans] filterbank.  subband=(S, G)
     dedisperses with the sub-band variant's effective table (subband_delays);
-    width_sigma=True normalises every width by its own sigma (width_sigma())."""
+    width_sigma=True normalises every width by its own sigma (width_sigma());
+    decimate=R evaluates widths W > R that are multiples of R only at the starts
+    m * W / R (decimated boxcars)."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     nsamps, nch = x.shape
     p, keep = _params(nch, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_mode,
-                      baseline_s, dm_tol, t_gap, w_tol, subband, width_sigma)
+                      baseline_s, dm_tol, t_gap, w_tol, subband, width_sigma, decimate)
     ndm = keep[0].size
     raw = np.empty(cap, dtype=RAW_DTYPE)
     cl = np.empty(cap, dtype=CLUSTER_DTYPE)
@@ -317,12 +319,12 @@ def search(x: np.ndarray, f_top, chan_bw, tsamp, dm_list, widths, thr, baseline_
 
 
 def search_trials(D: np.ndarray, d_begin: int, tsamp, widths, thr, baseline_mode=0,
-                  baseline_s=2.0, cap=1 << 22, width_sigma=False):
+                  baseline_s=2.0, cap=1 << 22, width_sigma=False, decimate=0):
     """Per-trial stages (baseline, sigma, boxcars, peaks) on dedispersed rows."""
     D = np.ascontiguousarray(D, dtype=np.int32)
     nrows, nout = D.shape
     p, keep = _params(1, 1500.0, -1.0, tsamp, np.zeros(1, np.float32), widths, thr,
-                      baseline_mode, baseline_s, 1, 0, None, None, width_sigma)
+                      baseline_mode, baseline_s, 1, 0, None, None, width_sigma, decimate)
     raw = np.empty(cap, dtype=RAW_DTYPE)
     sig = np.empty(nrows, dtype=np.float64)
     md = np.empty(nrows, dtype=np.int64)

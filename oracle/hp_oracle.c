@@ -30,6 +30,8 @@
  *   hpo_width_sigma       pinned: numpy brute force, W = 1 reduction to the MAD,
  *                                 sqrt(W) law on white noise, random-walk growth,
  *                                 rectangular pulse S/N by hand
+ *   decimated boxcars     pinned: numpy brute force on the scrunched series, R >= Wmax
+ *                                 reduction to every start
  */
 #include <math.h>
 #include <stdint.h>
@@ -378,12 +380,20 @@ static int raw_push(raw_vec* rv, hpo_raw r) {
     return 0;
 }
 
+/* Decimated boxcars, a variant the paper does not use (Heimdall scrunches the
+ * series for its wide boxcars): with a decimation R > 0, a width W > R that is
+ * a multiple of R is evaluated only at the starts t = m q, q = W / R, which is
+ * the boxcar of R samples on the series summed in blocks of q; its runs are
+ * maximal sets of consecutive grid starts above threshold.  Other widths keep
+ * every start (q = 1).  The sigmas are not changed by it. */
+static int64_t decim_step(int64_t W, int R) { return (R > 0 && W > R && W % R == 0) ? W / R : 1; }
+
 /* sigma_w: NULL for the paper's reading (one sigma per trial, scaled by
  * sqrt(W)), else the per-width sigmas of hpo_width_sigma: then the limit is
- * thr * sigma_w[k] and snr = S / sigma_w[k]. */
+ * thr * sigma_w[k] and snr = S / sigma_w[k].  decimate: R of decim_step. */
 static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
                        const int32_t* widths, int nw, float thr, const double* sigma_w,
-                       raw_vec* rv) {
+                       int decimate, raw_vec* rv) {
     if (!sigma_w && !(sigma > 0.0)) return 0;
     int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     if (!P) return -1;
@@ -397,17 +407,18 @@ static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
         double sw = sqrt((double)W);
         double lim = sigma_w ? thr_d * sigma_w[k] : thr_d * sigma * sw;
         int64_t last = n - W;
+        int64_t q = decim_step(W, decimate);   /* start grid step */
         int64_t t = 0;
         while (t <= last) {
             int64_t S = P[t + W] - P[t];
             if ((double)S >= lim) {
                 int64_t best_t = t, best_S = S;
-                ++t;
+                t += q;
                 while (t <= last) {
                     int64_t S2 = P[t + W] - P[t];
                     if (!((double)S2 >= lim)) break;
                     if (S2 > best_S) { best_S = S2; best_t = t; }
-                    ++t;
+                    t += q;
                 }
                 hpo_raw r;
                 r.dm_idx = d;
@@ -417,7 +428,7 @@ static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
                 r.snr = sigma_w ? (double)best_S / sigma_w[k] : (double)best_S / (sigma * sw);
                 if (raw_push(rv, r)) { free(P); return -1; }
             } else {
-                ++t;
+                t += q;
             }
         }
     }
@@ -430,7 +441,7 @@ int hpo_detect_trial(const int64_t* y, int64_t n, int d, double sigma,
                      const int32_t* widths, int nw, float thr,
                      hpo_raw* out, int64_t cap, int64_t* nout) {
     raw_vec rv = {0, 0, 0};
-    if (detect_into(y, n, d, sigma, widths, nw, thr, NULL, &rv)) { free(rv.v); return HPO_ERR_ARG; }
+    if (detect_into(y, n, d, sigma, widths, nw, thr, NULL, 0, &rv)) { free(rv.v); return HPO_ERR_ARG; }
     *nout = rv.n;
     int64_t m = rv.n < cap ? rv.n : cap;
     if (m > 0) memcpy(out, rv.v, sizeof(hpo_raw) * (size_t)m);
@@ -647,6 +658,7 @@ typedef struct {
     int subband_chans;   /* S of the sub-band variant; 0 = direct dedispersion */
     int subband_group;   /* G of the sub-band variant */
     int width_sigma;     /* 1 = per-width sigmas (hpo_width_sigma) */
+    int decimate;        /* R of the decimated boxcars (decim_step); 0 = every start */
 } hpo_params;
 
 /* The delay table a search dedisperses with: step c1's, or the sub-band
@@ -702,7 +714,8 @@ int hpo_search_trials(const int32_t* D /* [nrows][nout] */, int64_t nout, int d_
             sw = (double*)malloc(sizeof(double) * (size_t)(p->nw > 0 ? p->nw : 1));
             if (!sw || hpo_width_sigma(y, nout, p->widths, p->nw, NULL, sw)) bad = 1;
         }
-        if (!bad && detect_into(y, nout, d_begin + r, sigma, p->widths, p->nw, p->thr, sw, &per[r]))
+        if (!bad && detect_into(y, nout, d_begin + r, sigma, p->widths, p->nw, p->thr, sw,
+                                p->decimate, &per[r]))
             bad = 1;
         free(sw);
         free(y);

@@ -66,13 +66,19 @@ MUTANTS = {
     "wsig_sqrt_kept": ("double lim = sigma_w ? thr_d * sigma_w[k] : thr_d * sigma * sw;",
                        "double lim = sigma_w ? thr_d * sigma_w[k] * sw : thr_d * sigma * sw;"),
     "wsig_starts_short": ("int64_t m = n - W + 1;", "int64_t m = n - W;"),
+    # decimated boxcars
+    "decim_no_grid": ("int64_t q = decim_step(W, decimate);", "int64_t q = 1;"),
+    "decim_double_step": ("W % R == 0) ? W / R : 1;", "W % R == 0) ? 2 * W / R : 1;"),
+    "decim_run_every_start": ("t += q;\n                while (t <= last) {",
+                              "t += 1;\n                while (t <= last) {"),
     "wsig_snr_sqrt": ("r.snr = sigma_w ? (double)best_S / sigma_w[k] :",
                       "r.snr = sigma_w ? (double)best_S / (sigma_w[k] * sqrt((double)widths[k])) :"),
 }
 
 # the pin files that each group of mutants is checked against
 PINS = {"rfi_": ["test_oracle_rfi.py"], "stream_": ["test_oracle_stream.py"],
-        "subband_": ["test_oracle_subband.py"], "wsig_": ["test_oracle_widthsigma.py"]}
+        "subband_": ["test_oracle_subband.py"], "wsig_": ["test_oracle_widthsigma.py"],
+        "decim_": ["test_oracle_decimate.py"]}
 DEFAULT_PINS = ["test_oracle_pins.py", "test_oracle_stream.py"]
 
 
