@@ -68,6 +68,10 @@ def parse():
                     help="channels per sub-band and trials per group of the variant")
     ap.add_argument("--no-width-sigma", action="store_true",
                     help="skip the per-width normalisation variant's line")
+    ap.add_argument("--no-decimate", action="store_true",
+                    help="skip the decimated-boxcar variant's line")
+    ap.add_argument("--decimate", type=int, default=16,
+                    help="R of the decimated-boxcar variant")
     ap.add_argument("--serve-beams", type=int, default=19)
     ap.add_argument("--serve-seconds", type=float, default=40.0,
                     help="seconds of real-time stream per beam")
@@ -467,6 +471,8 @@ def run_ours(args):
     if world == 1 and not args.no_width_sigma:
         line["width_sigma"] = run_width_sigma(args, hp, torch, stream, w, s, fb, cands, peaks,
                                               hbm_peak, dev_ms, stats)
+    if world == 1 and not args.no_decimate:
+        line["decimate"] = run_decimate(args, hp, torch, stream, w, s, fb, cands, dev_ms, stats)
     if world == 1 and not args.no_batch:
         del fb
         plan.close()
@@ -626,6 +632,57 @@ def run_width_sigma(args, hp, torch, stream, w, s, fb, direct_cands, peaks, hbm_
                           "note": "two histogram levels of exact radix selection per "
                                   "(trial, width): each rebuilds nw boxcar sums per sample "
                                   "from a shared-memory prefix and counts one digit"},
+    }
+
+
+# ------------------------------------------------ decimated boxcars
+def run_decimate(args, hp, torch, stream, w, s, fb, direct_cands, direct_ms, direct_stats):
+    """The decimated-boxcar variant (not the paper's method) on the same file:
+    widths W > R that are multiples of R tested on the start grid W / R only."""
+    o = w.obs
+    R = int(args.decimate)
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    plan.set_param("decimate", R)
+    plan.bind_workspace(o.nsamps)
+    nout = plan.nout(o.nsamps)
+    out = hp.new_cand_buf(1 << 16)
+    for _ in range(max(3, args.warmup)):
+        hp.hp_search(plan, fb, stream, out=out)
+    if hp.hp_plan_sync_status(plan, stream) != hp.HP_OK:
+        raise hp.HPError(hp.hp_plan_sync_status(plan, stream), "decimated warm-up")
+    cands = hp.cands_to_numpy(*out)
+    hp.hp_plan_stats(plan, reset=True)
+    plan.set_param("stage_timing", 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        hp.hp_search(plan, fb, stream, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    stats = hp.hp_plan_stats(plan, reset=True)
+    per = {k: v / args.steps for k, v in stats["stage_ms"].items()}
+    ratios = []
+    for p in s.pulses:
+        d0 = best_match_snr(p, direct_cands, w)
+        if d0 > 0:
+            ratios.append(best_match_snr(p, cands, w) / d0)
+    direct_search = direct_stats["stage_ms"]["search"] / max(1, direct_stats["stage_calls"]["search"])
+    plan.close()
+    return {
+        "what": "decimated boxcars (not the paper's method): widths W > R, multiples of R, "
+                "tested on the start grid m*W/R (boxcars of R samples on the series summed "
+                "in blocks of W/R)",
+        "R": R, "value": w.ndm * nout / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms,
+        "vs_direct_ms_per_step": direct_ms, "search_ms": per["search"],
+        "search_ms_direct": direct_search,
+        "gpu_launches_per_step": stats["kernel_launches"] / args.steps,
+        "clusters": int(len(cands)), "clusters_direct": int(len(direct_cands)),
+        "recovery": recovery_rates(w, s.pulses, cands),
+        "snr_vs_direct": {"min": min(ratios) if ratios else None,
+                          "median": float(np.median(ratios)) if ratios else None,
+                          "pulses": len(ratios)},
     }
 
 

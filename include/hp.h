@@ -156,6 +156,17 @@ int hp_plan_destroy(hp_plan* plan);
  * (a stream's sigmas are those of each searched buffer).  |S_k| must stay below 2^36 (series within +-2^21 for W <= 16384),
  * else HP_ERR_INVALID_ARG is latched.  hp_width_sigmas returns the sigmas. */
 #define HP_PARAM_WIDTH_SIGMA 14   /* 0 = one sigma per trial scaled by sqrt(W) (default), 1 = per width */
+/* Decimated boxcars, a variant the paper does not use (Heimdall scrunches the
+ * series for its wide boxcars): with HP_PARAM_DECIMATE = R > 0 a width W > R
+ * that is a multiple of R is tested only at the starts t = m q, q = W / R --
+ * the boxcar of R samples on the series summed in blocks of q; a run is a
+ * maximal set of consecutive grid starts above threshold, its candidate the
+ * grid start of largest S (ties: the earliest).  Thresholds and sigmas are
+ * unchanged (with HP_PARAM_WIDTH_SIGMA the per-width sigmas still count every
+ * start).  q <= 1024 (R >= widest boxcar / 1024); series within +-2^21 (the
+ * summed blocks are int32).  hp_search, hp_detect and batches follow it;
+ * streams refuse it. */
+#define HP_PARAM_DECIMATE 15      /* R: 0 = every start (default) */
 
 #define HP_NUM_DEDISP_CONFIGS 27
 

@@ -245,6 +245,18 @@ struct SearchArgs {
     WsigState* wstate;         // [ndm][nw]
     int64_t* wmad;             // [ndm][nw] lower median of |S_k|
     double* sigw;              // [ndm][nw] sigma_k
+    // reported samples are t * sample_mul + t_offset (1 but on a scrunched series)
+    int64_t sample_mul;
+    // decimated boxcars: widths W > decimate that are multiples of it run on the
+    // series summed in blocks of q = W / decimate; ndec distinct q (ascending),
+    // level l's series at ydec + dec_off[l] with pitch dec_pitch[l], thresholds
+    // tint_lv [ndec][ndm][nw], widths widths_lv [ndec][nw] (W / q, or 1)
+    int decimate, ndec;
+    int32_t dec_q[kMaxWidths];
+    int64_t dec_off[kMaxWidths], dec_pitch[kMaxWidths];
+    int32_t* ydec;
+    int64_t* tint_lv;
+    int32_t* widths_lv;
 };
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch);
 

@@ -494,6 +494,28 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
     L.mad = take((size_t)ndm * 8);
     L.sigma = take((size_t)ndm * 8);
     L.tint = take((size_t)ndm * p->nw() * 8);
+    if (p->decimate > 0) {
+        // the distinct block sizes q = W / R of the decimated widths, ascending,
+        // and one scrunched series per q
+        std::vector<int32_t> qs;
+        for (int32_t W : p->widths)
+            if (W > p->decimate && W % p->decimate == 0) qs.push_back(W / p->decimate);
+        std::sort(qs.begin(), qs.end());
+        qs.erase(std::unique(qs.begin(), qs.end()), qs.end());
+        L.ndec = (int)qs.size();
+        size_t bytes = 0;
+        for (int l = 0; l < L.ndec; ++l) {
+            L.dec_q[l] = qs[l];
+            L.dec_pitch[l] = round_up64(std::max<int64_t>(L.nout / qs[l], 1), 64);
+            L.dec_off[l] = (int64_t)(bytes / 4);
+            bytes += (size_t)ndm * L.dec_pitch[l] * 4;
+        }
+        if (L.ndec > 0) {
+            L.ydec = take(bytes);
+            L.tint_lv = take((size_t)L.ndec * ndm * p->nw() * 8);
+            L.widths_lv = take((size_t)L.ndec * p->nw() * 4);
+        }
+    }
     if (p->width_sigma) {
         const size_t pairs = (size_t)ndm * p->nw();
         L.whist = take(pairs * 2 * 4096 * 4);
@@ -789,6 +811,17 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.carry_out = nullptr;
     a.t_offset = 0;
     a.stats_only = 0;
+    a.sample_mul = 1;
+    a.decimate = p->decimate;
+    a.ndec = L.ndec;
+    for (int l = 0; l < L.ndec; ++l) {
+        a.dec_q[l] = L.dec_q[l];
+        a.dec_off[l] = L.dec_off[l];
+        a.dec_pitch[l] = L.dec_pitch[l];
+    }
+    a.ydec = L.ndec > 0 ? (int32_t*)(ws + L.ydec) : nullptr;
+    a.tint_lv = L.ndec > 0 ? (int64_t*)(ws + L.tint_lv) : nullptr;
+    a.widths_lv = L.ndec > 0 ? (int32_t*)(ws + L.widths_lv) : nullptr;
     a.width_sigma = p->width_sigma ? 1 : 0;
     a.whist = p->width_sigma ? (uint32_t*)(ws + L.whist) : nullptr;
     a.wstate = p->width_sigma ? (WsigState*)(ws + L.wstate) : nullptr;
@@ -849,6 +882,7 @@ RfiArgs make_rfi_args(hp_plan* p, const Layout& L, uint8_t* ws, const uint8_t* x
     z.ypitch = L.r_zpitch;
     z.nwin = nsamps;
     z.stats_only = 1;
+    z.sample_mul = 1;
     return r;
 }
 
@@ -1074,6 +1108,7 @@ std::vector<uintptr_t> batch_key(const hp_batch* b, const uint8_t* const* fbs,
         k.push_back((uintptr_t)(p->rfi_bb_k * 1e6));
         k.push_back((uintptr_t)p->width_sigma);
         k.push_back((uintptr_t)p->sb_chans);
+        k.push_back((uintptr_t)p->decimate);
         k.push_back((uintptr_t)p->sb_group);
     }
     return k;
@@ -1204,6 +1239,11 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
             if (!(v > 0.0) || v > 1e6) return HP_ERR_INVALID_ARG;
             p->rfi_bb_k = (float)v;
             return HP_OK;
+        case HP_PARAM_DECIMATE:
+            // a block size q = W / R of at most 1024 keeps the summed series int32
+            if (v < 0 || v != std::floor(v) || (v > 0 && p->wmax / v > 1024)) return HP_ERR_INVALID_ARG;
+            p->decimate = (int)v;
+            return HP_OK;
         case HP_PARAM_WIDTH_SIGMA:
             if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
             p->width_sigma = v == 1.0;
@@ -1242,6 +1282,7 @@ int hp_plan_get_param(const hp_plan* p, int param, double* v) {
         case HP_PARAM_RFI_BB_K: *v = (double)p->rfi_bb_k; return HP_OK;
         case HP_PARAM_SUBBAND_CHANS: *v = p->sb_chans; return HP_OK;
         case HP_PARAM_WIDTH_SIGMA: *v = p->width_sigma ? 1.0 : 0.0; return HP_OK;
+        case HP_PARAM_DECIMATE: *v = p->decimate; return HP_OK;
         case HP_PARAM_SUBBAND_GROUP: *v = p->sb_group; return HP_OK;
         default: return HP_ERR_INVALID_ARG;
     }

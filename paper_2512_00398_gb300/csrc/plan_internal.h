@@ -29,6 +29,10 @@ struct Layout {
            r_mad = 0, r_sigma = 0, r_tint = 0, r_y = 0;
     int64_t r_zpitch = 0, r_lvl_pitch_a = 0, r_lvl_pitch_b = 0, r_mean_pitch = 0;
     size_t whist = 0, wstate = 0, wmad = 0, sigw = 0;   // per-width sigmas (if enabled)
+    size_t ydec = 0, tint_lv = 0, widths_lv = 0;         // decimated boxcars (if enabled)
+    int ndec = 0;
+    int32_t dec_q[kMaxWidths] = {};
+    int64_t dec_off[kMaxWidths] = {}, dec_pitch[kMaxWidths] = {};
     size_t sb = 0;             // sub-band partial sums (sub-band variant)
     int64_t sb_pitch = 0, sb_len = 0;
     int sb_chunks = 0;         // DM-tile chunks whose partial sums fit `sb` at once
@@ -86,6 +90,7 @@ struct hp_plan {
 
     // device allocator for the plan's tables and workspace (default cudaMalloc)
     bool width_sigma = false;      // per-width sigmas instead of sigma * sqrt(W)
+    int decimate = 0;              // decimated boxcars: R (0 = every start)
     const double* last_sigw = nullptr;   // where the last search put them ([ndm][nw])
     const int64_t* last_wmad = nullptr;
     bool rfi = false;              // RFI mitigation before dedispersion

@@ -445,7 +445,7 @@ __device__ __forceinline__ void emit(const SearchArgs& a, int trial, int k, int6
         hp_raw_cand c;
         c.dm_idx = trial;
         c.width_idx = k;
-        c.sample = t + a.t_offset;
+        c.sample = t * a.sample_mul + a.t_offset;
         c.S = S;
         a.raw[idx] = c;
     }
@@ -930,6 +930,55 @@ cudaError_t launch_width_sigma(const SearchArgs& a, cudaStream_t s, int64_t* nla
 }
 
 
+// ------------------------------------------------- decimated boxcars
+// Thresholds of the decimated widths move to their level's table (kNever in
+// the every-start pass); level l takes the widths with W / decimate == dec_q[l]
+// as boxcars of W / q samples on its scrunched series.
+__global__ void decim_split_kernel(const __grid_constant__ SearchArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)a.ndm * a.nw) return;
+    const int k = (int)(i % a.nw);
+    const int32_t W = a.widths[k];
+    const int32_t q = (W > a.decimate && W % a.decimate == 0) ? W / a.decimate : 1;
+    const int64_t thr = a.tint[i];
+    for (int l = 0; l < a.ndec; ++l) {
+        a.tint_lv[(int64_t)l * a.ndm * a.nw + i] = q == a.dec_q[l] ? thr : kNever;
+        if (i < a.nw) a.widths_lv[(int64_t)l * a.nw + k] = q == a.dec_q[l] ? W / q : 1;
+    }
+    if (q > 1) a.tint[i] = kNever;
+}
+
+// dst[d][m] = sum of src[d][m f .. m f + f), m < n_dst (int32: |y| < 2^21 and
+// f * q <= 1024 keep the sums below 2^31)
+__global__ void __launch_bounds__(256) scrunch_kernel(const int32_t* __restrict__ src,
+                                                      int64_t src_pitch, int64_t n_src, int f,
+                                                      int32_t* __restrict__ dst, int64_t dst_pitch,
+                                                      int64_t n_dst) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (m >= n_dst || (m + 1) * f > n_src) return;
+    const int32_t* r = src + (int64_t)d * src_pitch + m * f;
+    int64_t acc = 0;
+    for (int i = 0; i < f; ++i) acc += r[i];
+    dst[(int64_t)d * dst_pitch + m] = (int32_t)acc;
+}
+
+cudaError_t launch_detect(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch) {
+    cudaError_t e;
+    if (a.nout <= 0) return cudaSuccess;
+    const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
+    if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const dim3 dgrid((unsigned)ceil_div(a.nout, kDetectTile), a.ndm);
+    ++*nlaunch;
+    detect_kernel<<<dgrid, kDetectThreads, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nlaunch;
+    tail_kernel<<<64, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStream_t s,
                            int64_t* nlaunch) {
@@ -958,17 +1007,39 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.stats_only) return cudaSuccess;
     if (a.width_sigma && (e = launch_width_sigma(a, s, nlaunch)) != cudaSuccess) return e;
-    const size_t smem = ((size_t)kDetectTile + (size_t)a.wmax + 2) * sizeof(int64_t);
-    if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    const dim3 dgrid((unsigned)ceil_div(n, kDetectTile), ndm);
-    ++*nlaunch;
-    detect_kernel<<<dgrid, kDetectThreads, smem, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nlaunch;
-    tail_kernel<<<64, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.ndec > 0) {
+        // the decimated widths leave the every-start pass for their own levels
+        ++*nlaunch;
+        decim_split_kernel<<<(unsigned)ceil_div((int64_t)ndm * a.nw, 256), 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = launch_detect(a, s, nlaunch)) != cudaSuccess) return e;
+    for (int l = 0; l < a.ndec; ++l) {
+        // series summed in blocks of q, from the previous level when q divides
+        const int q = a.dec_q[l];
+        const int qp = l > 0 && q % a.dec_q[l - 1] == 0 ? a.dec_q[l - 1] : 1;
+        const int32_t* src = qp > 1 ? a.ydec + a.dec_off[l - 1] : a.Y;
+        const int64_t src_pitch = qp > 1 ? a.dec_pitch[l - 1] : a.ypitch;
+        const int64_t n_src = n / qp, n_l = n / q;
+        ++*nlaunch;
+        scrunch_kernel<<<dim3((unsigned)ceil_div(n_l, 256), ndm), 256, 0, s>>>(
+            src, src_pitch, n_src, q / qp, a.ydec + a.dec_off[l], a.dec_pitch[l], n_l);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        SearchArgs al = a;
+        al.Y = a.ydec + a.dec_off[l];
+        al.ypitch = a.dec_pitch[l];
+        al.nout = n_l;
+        al.nwin = n_l;
+        al.widths = a.widths_lv + (int64_t)l * a.nw;
+        al.wmax = a.decimate;
+        al.tint = a.tint_lv + (int64_t)l * ndm * a.nw;
+        al.sample_mul = q;
+        al.carry_in = nullptr;
+        al.carry_out = nullptr;
+        if ((e = cudaMemsetAsync(a.tail_count, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+        if ((e = launch_detect(al, s, nlaunch)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace

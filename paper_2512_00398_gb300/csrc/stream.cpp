@@ -446,6 +446,7 @@ int hp_stream_open(hp_stream** out, const hp_plan* tmpl, const hp_stream_config*
     if (!out) return HP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!tmpl || !cfg) return HP_ERR_INVALID_ARG;
+    if (tmpl->decimate > 0) return HP_ERR_INVALID_ARG;   // every start in a stream's window
     if (cfg->nbeams < 1 || cfg->nbeams > HP_STREAM_MAX_BEAMS) return HP_ERR_INVALID_ARG;
     if (cfg->max_batch < 0 || cfg->max_batch > HP_BATCH_MAX_FILES) return HP_ERR_INVALID_ARG;
     if (cfg->gulp < 64 || cfg->gulp >= kMaxSamples / 4) return HP_ERR_INVALID_ARG;

@@ -245,3 +245,19 @@ def test_dedisp_config_shapes():
     for bad in (-1, hp.HP_NUM_DEDISP_CONFIGS):
         with pytest.raises(hp.HPError):
             hp.hp_dedisp_config(bad)
+
+
+def test_decimate_param():
+    w = workloads.fast(nsamps=1 << 17)       # widths up to 4096
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold) as p:
+        assert p.get_param("decimate") == 0
+        base = p.workspace_bytes(1 << 20)
+        p.set_param("decimate", 16)
+        assert p.get_param("decimate") == 16
+        # scrunched series for q = 2 .. 256 (widths 32 .. 4096): under the size of y
+        extra = p.workspace_bytes(1 << 20) - base
+        assert 0 < extra < w.ndm * (1 << 20) * 4 * 1.05
+        for bad in (-1, 2.5, 2):          # 4096 / 2 > 1024 blocks per sample
+            with pytest.raises(hp.HPError):
+                p.set_param("decimate", bad)

@@ -1,0 +1,92 @@
+"""Decimated boxcars (HP_PARAM_DECIMATE) on the GPU against the oracle.
+
+The wide widths run as boxcars of R samples on the series summed in blocks of
+W / R; their candidates must be the oracle's (tuples and sums exact, samples on
+the start grid), alone, with per-width sigmas, from hp_detect, in batches.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+SNR_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def hp():
+    import paper_2512_00398_gb300 as hp
+    return hp
+
+
+def _plan(hp, w, **params):
+    o = w.obs
+    return hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                   **params)
+
+
+@pytest.fixture(scope="module")
+def tiny(torch):
+    from paper_2512_00398_gb300 import workloads
+    w = workloads.tiny()
+    s = w.generate()
+    return w, s, torch.from_numpy(s.data).cuda()
+
+
+def _same_clusters(got, want):
+    key = lambda c: (int(c["dm_idx"]), int(c["sample"]), int(c["width_idx"]))
+    assert [key(c) for c in got] == [key(c) for c in want]
+    for a, b in zip(got, want):
+        assert abs(float(a["snr"]) - float(b["snr"])) <= SNR_TOL
+        for f in ("members", "dm_lo", "dm_hi", "t_lo", "t_hi"):
+            assert int(a[f]) == int(b[f])
+
+
+@pytest.mark.parametrize("R", [2, 8, 32])
+@pytest.mark.parametrize("width_sigma", [0, 1])
+def test_search_matches_oracle(hp, torch, tiny, R, width_sigma):
+    w, s, fb = tiny
+    o = w.obs
+    want = oracle.search(s.data, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                         decimate=R, width_sigma=bool(width_sigma))
+    got = hp.search(_plan(hp, w, decimate=R, width_sigma=width_sigma), fb)
+    assert len(want.clusters) > 0
+    _same_clusters(got, want.clusters)
+
+
+def test_detect_raw_exact_on_the_grid(hp, torch, tiny):
+    w, s, fb = tiny
+    o = w.obs
+    D = oracle.dedisperse(s.data, oracle.delays(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list))
+    R = 4
+    raw_g, _, _ = hp.detect(_plan(hp, w, decimate=R), torch.from_numpy(D).cuda(), D.shape[1])
+    raw_o, _, _ = oracle.search_trials(D, 0, o.tsamp, w.widths, w.threshold, decimate=R)
+    key = lambda rows: sorted((int(r["dm_idx"]), int(r["sample"]), int(r["width_idx"]), int(r["S"]))
+                              for r in rows)
+    assert key(raw_g) == key(raw_o) and len(raw_o) > 0
+    for r in raw_g:
+        W = int(w.widths[r["width_idx"]])
+        if W > R:
+            assert int(r["sample"]) % (W // R) == 0
+
+
+def test_batch_and_refusals(hp, torch, tiny):
+    w, s, fb = tiny
+    want = hp.search(_plan(hp, w, decimate=8), fb)
+    b = hp.Batch([_plan(hp, w, decimate=8)])
+    for _ in range(3):
+        assert np.array_equal(b.search([fb])[0], want)
+    b.close()
+    with pytest.raises(hp.HPError):
+        hp.Stream(_plan(hp, w, decimate=8), nbeams=1, gulp=4096)
+    with pytest.raises(hp.HPError):
+        _plan(hp, w, decimate=-1)
