@@ -90,3 +90,22 @@ def test_batch_and_refusals(hp, torch, tiny):
         hp.Stream(_plan(hp, w, decimate=8), nbeams=1, gulp=4096)
     with pytest.raises(hp.HPError):
         _plan(hp, w, decimate=-1)
+
+
+def test_all_variants_together(hp, torch, tiny):
+    """RFI mitigation, sub-band dedispersion, per-width sigmas and decimated
+    boxcars at once: the oracle cleans, dedisperses with the effective table,
+    normalises per width and tests the wide widths on their grids."""
+    w, s, fb = tiny
+    o = w.obs
+    x = s.data.astype(np.int32)
+    x[:, [9, 60]] += 50
+    x[::3100, :] += 45
+    x = np.clip(x, 0, 255).astype(np.uint8)
+    clean = oracle.rfi_clean(x, o.tsamp).cleaned
+    want = oracle.search(clean, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                         subband=(32, 4), width_sigma=True, decimate=8)
+    p = _plan(hp, w, rfi=1, subband_chans=32, subband_group=4, width_sigma=1, decimate=8)
+    got = hp.search(p, torch.from_numpy(x).cuda())
+    assert len(want.clusters) > 0
+    _same_clusters(got, want.clusters)
