@@ -109,3 +109,23 @@ def test_all_variants_together(hp, torch, tiny):
     got = hp.search(p, torch.from_numpy(x).cuda())
     assert len(want.clusters) > 0
     _same_clusters(got, want.clusters)
+
+
+def test_block_sizes_that_do_not_chain(hp, torch):
+    """Widths 5, 10, 15, 30 with R = 5: block sizes 2, 3 and 6 -- the series
+    for 3 is summed from y itself (3 is not a multiple of 2), the one for 6 from
+    the series for 3."""
+    rng = np.random.default_rng(17)
+    nout, ndm = 30011, 3
+    widths = np.array([1, 5, 10, 15, 30], np.int32)
+    D = np.rint(rng.normal(5000, 30, (ndm, nout))).astype(np.int32)
+    D[0, 7000:7030] += 60
+    D[1, 12000:12011] += 90
+    D[2, 20000:20090] += 25
+    p = hp.Plan(64, 1500.0, -1.0, 1e-3, np.zeros(ndm, np.float32), widths, 6.0, decimate=5)
+    raw_g, _, _ = hp.detect(p, torch.from_numpy(D).cuda(), nout)
+    raw_o, _, _ = oracle.search_trials(D, 0, 1e-3, widths, 6.0, decimate=5)
+    key = lambda rows: sorted((int(r["dm_idx"]), int(r["sample"]), int(r["width_idx"]), int(r["S"]))
+                              for r in rows)
+    assert key(raw_g) == key(raw_o) and len(raw_o) > 0
+    assert {int(r["width_idx"]) for r in raw_o} >= {2, 3}
