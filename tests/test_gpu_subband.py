@@ -214,3 +214,20 @@ def test_subband_search_with_rfi_matches_oracle(hp, torch, tiny):
     assert [key(c) for c in got] == [key(c) for c in want.clusters]
     for a, b in zip(got, want.clusters):
         assert abs(float(a["snr"]) - float(b["snr"])) <= SNR_TOL
+
+
+def test_subband_shortest_input(hp, torch, tiny):
+    """The shortest accepted input (nsamps = max effective delay + widest boxcar + 1)
+    and one sample less (refused)."""
+    w, s, fb, tab = tiny
+    o = w.obs
+    p = _plan(hp, w, subband_chans=16, subband_group=4)
+    eff = p.delays()
+    n = int(eff.max()) + int(w.widths.max()) + 1
+    x = s.data[:n]
+    got = hp.dedisperse(p, torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    assert got.shape[1] == n - int(eff.max())
+    assert np.array_equal(got, oracle.dedisperse(x, eff))
+    with pytest.raises(hp.HPError) as e:
+        hp.search(p, torch.from_numpy(np.ascontiguousarray(s.data[:n - 1])).cuda())
+    assert e.value.code == hp.HP_ERR_NSAMPS_TOO_SHORT
