@@ -9,8 +9,8 @@
  * Every step follows the pipeline of Section II-B (stage list) and Algorithm 1
  * (per-trial loop: baseline removal, normalisation, matched filtering, peak
  * detection; then merging/clustering).  The paper names the stages but prints
- * no formulas except the DM integral (Eq. 1); the readings used where it is
- * silent are listed next to each function and in the design doc.
+ * no formulas except the DM integral (Eq. 1); the reading used where it is
+ * silent is written out next to each function.
  *
  * Arithmetic: exact integers (int64) for every sum; FP64 for sigma, the
  * threshold and S/N.  Build with -ffp-contract=off so that no multiply-add
