@@ -37,13 +37,13 @@ METRIC = "DM-trial·samples/s"
 # capture of the full-size bench command (profiles/dedisp_rows_kernel_fast_4096ch.md).
 # Keyed by the kernel source it was measured on; a changed kernel, another workload or
 # another configuration reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "fb7f99522ade5692", "bytes": 37.60e9 + 5.74e9,
+DEDISP_TRAFFIC = {"source_sha256_16": "203cb08ce13500ce", "bytes": 37.88e9 + 5.74e9,
                   "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22}
 # The same for the two stages of the sub-band variant (64-channel sub-bands, groups
 # of 8 trials): DRAM bytes of one step (4 launches of each stage), measured per launch
 # (profiles/subband_fast_4096ch.md), keyed by both kernel sources.
-SUBBAND_TRAFFIC = {"source_sha256_16": "fb7f99522ade5692+6752b94441917dc0",
-                   "stage1": 4 * (8.64e9 + 12.80e9), "stage2": 4 * (11.75e9 + 1.45e9),
+SUBBAND_TRAFFIC = {"source_sha256_16": "203cb08ce13500ce+6752b94441917dc0",
+                   "stage1": 31.98e9 + 46.35e9, "stage2": 46.04e9 + 5.67e9,
                    "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22, "S": 64, "G": 8}
 
 
@@ -538,8 +538,19 @@ def run_subband(args, hp, torch, stream, w, s, fb, direct_cands, peaks, hbm_peak
             ratios.append(best_match_snr(p, cands, w) / d0)
     nsub = -(-o.nchans // S)
     ngrp = -(-w.ndm // G)
-    sb_len = nout + int(plan.delays()[:, ::S].max())
-    adds1 = float(o.nchans) * ngrp * sb_len          # stage 1: byte-adds at the nominal trials
+    eff = plan.delays()
+    top = eff[:, ::S].astype(np.int64)               # delay of each sub-band's first channel
+    sb_len = nout + int(top.max())
+    # stage 1: byte-adds at the nominal trials, each sub-band of each chunk of groups
+    # over the samples stage 2 reads from it (nout + its largest first-channel delay)
+    shape = hp.hp_dedisp_config(int(plan.get_param("dedisp_config")))
+    gchunk = shape["RD"] * shape["WD"]                 # nominal trials per chunk
+    widths_s = np.minimum(S, o.nchans - np.arange(nsub) * S)
+    adds1 = 0.0
+    for g0 in range(0, ngrp, gchunk):
+        nd = min(gchunk, ngrp - g0)
+        d_last = min((g0 + nd) * G, w.ndm) - 1
+        adds1 += float(nd) * float(np.sum(widths_s * (nout + top[d_last])))
     adds2 = float(w.ndm) * nsub * nout               # stage 2: int32 adds of partial sums
     bytes2 = 4.0 * nsub * ngrp * sb_len + 4.0 * w.ndm * nout
     peak_adds = 2.0 * peaks["int_add_ops_per_s"]
@@ -560,8 +571,10 @@ def run_subband(args, hp, torch, stream, w, s, fb, direct_cands, peaks, hbm_peak
                             "achieved": adds1 / (t1 * 1e-3) / 1e12, "peak": peak_adds / 1e12,
                             "unit": "Tadd/s", "frac": adds1 / (t1 * 1e-3) / peak_adds,
                             "traffic": tr1,
-                            "algorithmic": f"{o.nchans} ch x {ngrp} nominal trials x {sb_len} "
-                                           f"samples = {adds1:.3e} byte-adds per step"},
+                            "algorithmic": f"{o.nchans} ch x {ngrp} nominal trials x (nout + the "
+                                           f"sub-band's largest first-channel delay in its "
+                                           f"chunk, at most {sb_len}) samples = {adds1:.3e} "
+                                           f"byte-adds per step"},
         "stage2_roofline": {"bound": "hbm", "kernel": "subband_sum_kernel",
                             "achieved": bytes2 / (t2 * 1e-3) / 1e9, "peak": hbm_peak,
                             "unit": "GB/s", "frac": bytes2 / (t2 * 1e-3) / 1e9 / hbm_peak,

@@ -891,11 +891,18 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
 
     if (warp == NCW) {
         // ------------------------------------------------------- producer
-        int issued = 0;
+        int issued = 0, used = 0;
         for (int s = 0; s < nst; ++s) {
-            const int b = s % NB;
-            if (s >= NB &&
-                !__all_sync(0xffffffffu, mbar_wait_or_abort(&empty[b], (uint32_t)(s / NB - 1) & 1u,
+            // q: the ring position (SEG: stages of segments this time tile does not
+            // need are skipped by the producer and the consumers alike)
+            int q = s;
+            if constexpr (SEG) {
+                if (t0 >= J.nout - (int64_t)(J.stages[T.stage_begin + s].seg_info >> 1)) continue;
+                q = used++;
+            }
+            const int b = q % NB;
+            if (q >= NB &&
+                !__all_sync(0xffffffffu, mbar_wait_or_abort(&empty[b], (uint32_t)(q / NB - 1) & 1u,
                                                             timeout_ns, abort)))
                 break;
             const StageDesc S = J.stages[T.stage_begin + s];
@@ -912,7 +919,7 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
                 const uint8_t* src = J.xt + (int64_t)cd.c * J.xt_pitch + t0 + cd.goff;
                 bulk_copy_g2s(B + cd.offB, src, 4 * cd.nwords, &full[b]);
             }
-            issued = s + 1;
+            issued = q + 1;
         }
         if (lane == 0 && *abort) {
             latch_status(status, HP_ERR_TIMEOUT);
@@ -961,10 +968,16 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
         }
     };
     uint32_t held = 0;
+    int used = 0;
     for (int s = 0; s < nst; ++s) {
-        const int b = s % NB;
+        int q = s;
+        if constexpr (SEG) {
+            if (t0 >= J.nout - (int64_t)(J.stages[T.stage_begin + s].seg_info >> 1)) continue;
+            q = used++;
+        }
+        const int b = q % NB;
         if (!__all_sync(0xffffffffu,
-                        mbar_wait_or_abort(&full[b], (uint32_t)(s / NB) & 1u, timeout_ns, abort)))
+                        mbar_wait_or_abort(&full[b], (uint32_t)(q / NB) & 1u, timeout_ns, abort)))
             return;
         const uint32_t B = sbase + (uint32_t)(b * stage_bytes);
         const StageDesc S = J.stages[T.stage_begin + s];
@@ -1004,7 +1017,7 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
         held += nchan;
-        const bool seg_end = SEG && S.seg_end != 0u;
+        const bool seg_end = SEG && (S.seg_info & 1u) != 0u;
         const uint32_t next_n = s + 1 < nst ? J.stages[T.stage_begin + s + 1].nchan : 256u;
         if (seg_end || held + next_n > 256u) {
             held = 0;

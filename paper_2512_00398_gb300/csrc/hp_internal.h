@@ -70,8 +70,10 @@ struct StageDesc {
     // Segments (sub-band stage 1, byte-row kernel): the tile's channels are cut
     // into segments that no stage straddles; after the last stage of a segment
     // the block writes its sums to rows seg_row + trial and starts from zero.
+    // seg_info: bit 0 = last stage of its segment; bits 1.. = trim: the segment's
+    // rows are needed only below nout - trim, so time tiles from there on skip it.
     int32_t seg_row;
-    uint32_t seg_end;     // 1 on the last stage of a segment
+    uint32_t seg_info;
 };
 static_assert(sizeof(StageDesc) == 32, "StageDesc layout");
 
@@ -145,7 +147,8 @@ cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8
 cudaError_t launch_dedisp(int cfg, const DedispBatch& batch, int* status, uint64_t timeout_ns,
                           cudaStream_t s);
 // The same tilings run segment by segment (stage 1 of the sub-band variant):
-// rows are written at the end of every segment (StageDesc::seg_row / seg_end).
+// rows are written at the end of every segment (StageDesc::seg_row / seg_info)
+// and time tiles past a segment's needed length skip its stages.
 // Byte-row configs for which segmented_config() holds only.
 bool segmented_config(int cfg);
 cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& batch, int* status,

@@ -159,11 +159,12 @@ uint32_t stage_header(int nchan, int BD, int layout) {
 // Stages, channel descriptors and address tables of one DM tile of nd trials
 // whose delay of trial j in channel c is delay(j, c); channels [0, nch) are
 // cut at seg_begin[i] into segments that no stage straddles, the trials of
-// segment i being written to rows seg_row[i] + j.
+// segment i being written to rows seg_row[i] + j for output samples below
+// nout - seg_trim[i].
 template <class Delay>
 int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg_begin,
-                const std::vector<int32_t>& seg_row, int32_t d0, const DedispConfig& C,
-                DedispTiling* T) {
+                const std::vector<int32_t>& seg_row, const std::vector<uint32_t>& seg_trim,
+                int32_t d0, const DedispConfig& C, DedispTiling* T) {
     const int BD = C.BD(), BT = C.BT();
     const uint32_t budget = (uint32_t)C.stage_bytes;
     std::vector<RowGeom> geo_all(nch);
@@ -201,7 +202,7 @@ int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg
             sd.addr_begin = (uint32_t)T->addr.size();
             sd.addr_bytes = stage_table_bytes(n, BD, C.layout);
             sd.seg_row = seg_row[sg];
-            sd.seg_end = c + n == c_end ? 1u : 0u;
+            sd.seg_info = (seg_trim[sg] << 1) | (c + n == c_end ? 1u : 0u);
             uint32_t off = stage_header(n, BD, C.layout);
             uint32_t tx = (uint32_t)(n * sizeof(ChanDesc)) + sd.addr_bytes;
             std::vector<uint32_t> word0(n);   // per channel: byte offset of row copy 0
@@ -304,7 +305,14 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                 const int32_t* row = &p->delays[(size_t)sb_nominal(p, (g0 + j) * p->sb_group) * nch];
                 return row[c] - row[(c / S) * S];
             };
-            const int rc = append_tile(delay, nd, nch, seg_begin, seg_row, 0, C, T);
+            // stage 2 reads a sub-band's partial sums below nout + the largest delay
+            // of its first channel over the chunk's trials; stage 1 runs over
+            // nout + sb_maxtop samples, so each sub-band may stop sb_maxtop - that early
+            const int d_last = std::min((g0 + nd) * p->sb_group, p->ndm()) - 1;
+            std::vector<uint32_t> seg_trim;
+            for (int s = 0; s < p->sb_nsub; ++s)
+                seg_trim.push_back((uint32_t)(p->sb_maxtop - p->delays[(size_t)d_last * nch + s * S]));
+            const int rc = append_tile(delay, nd, nch, seg_begin, seg_row, seg_trim, 0, C, T);
             if (rc) return rc;
         }
         T->cfg = cfg;
@@ -323,7 +331,7 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
         }
         const int32_t* base = &p->delays[(size_t)d0 * nch];
         auto delay = [&](int j, int c) { return base[(size_t)j * nch + c]; };
-        const int rc = append_tile(delay, nd, nch, {0}, {d0}, d0, C, T);
+        const int rc = append_tile(delay, nd, nch, {0}, {d0}, {0u}, d0, C, T);
         if (rc) return rc;
         d0 += nd;
     }
