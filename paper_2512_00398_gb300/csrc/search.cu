@@ -59,7 +59,20 @@ __global__ void __launch_bounds__(256) remedian_pass_kernel(const int32_t* __res
     const int64_t base = (int64_t)blockIdx.x * chunk;
     int cnt = (int)min(chunk, n_in - base);
     const int32_t* src = in + (int64_t)trial * in_pitch + base;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) buf[0][i] = src[i];
+    constexpr int kLoadBatch = 8;   // independent loads in flight per thread
+    for (int ib = threadIdx.x; ib < cnt; ib += kLoadBatch * blockDim.x) {
+        int32_t v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int i = ib + u * (int)blockDim.x;
+            v[u] = i < cnt ? __ldg(src + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int i = ib + u * (int)blockDim.x;
+            if (i < cnt) buf[0][i] = v[u];
+        }
+    }
     __syncthreads();
     int cur = 0;
     for (int l = 0; l < q; ++l) {
@@ -250,7 +263,7 @@ __device__ __forceinline__ void load_chunk32(const int32_t* __restrict__ row, in
 // for the passes after it.  Each thread reads its whole chunk before it
 // writes, so Y may alias D (median mode, whose walker reads only the knots).
 template <int MODE>
-__global__ void __launch_bounds__(256) mad_hist_kernel(const int32_t* D, int64_t pitch, int64_t n,
+__global__ void __launch_bounds__(256, 3) mad_hist_kernel(const int32_t* D, int64_t pitch, int64_t n,
                                                        BaselineCtx bc, int vec,
                                                        uint32_t* __restrict__ hist, int32_t* Y,
                                                        int64_t ypitch, int yvec) {
@@ -500,27 +513,44 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t warp_max[32];
     __shared__ unsigned above_bits[kDetectThreads / 32][kDetectPer];
+    __shared__ int64_t thr_s[kMaxWidths];     // this trial's integer thresholds
+    __shared__ int32_t width_s[kMaxWidths];
     const int trial = blockIdx.y;
     const int64_t n = a.nout;
     const int64_t t0 = (int64_t)blockIdx.x * kDetectTile;
     const int64_t base = t0 - 1;
-    const int64_t len = min((int64_t)kDetectTile + a.wmax, n - base);
+    const int len = (int)min((int64_t)kDetectTile + a.wmax, n - base);   // <= tile + kMaxWidth
     const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < a.nw) {
+        thr_s[tid] = a.tint[(int64_t)trial * a.nw + tid];
+        width_s[tid] = a.widths[tid];
+    }
 
-    // y over [base, base + len) into P[1 ..] with coalesced loads (the slot
-    // before sample 0 holds y = 0), then one contiguous chunk per thread (an odd
-    // chunk length keeps the 16 threads of a half-warp on distinct banks) and a
-    // block prefix sum
-    for (int64_t i = tid; i < len; i += kDetectThreads) {
-        const int64_t s = base + i;
-        P[i + 1] = s < 0 ? 0 : (int64_t)yrow[s];
+    // y over [base, base + len) into P[1 ..] with coalesced loads, a batch of
+    // independent loads in flight per thread (the slot before sample 0 holds
+    // y = 0), then one contiguous chunk per thread (an odd chunk length keeps
+    // the 16 threads of a half-warp on distinct banks) and a block prefix sum
+    constexpr int kLoadBatch = 8;
+    for (int ib = tid; ib < len; ib += kLoadBatch * kDetectThreads) {
+        int32_t v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int i = ib + u * kDetectThreads;
+            const int64_t s = base + i;
+            v[u] = (i < len && s >= 0) ? __ldg(yrow + s) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int i = ib + u * kDetectThreads;
+            if (i < len) P[i + 1] = (int64_t)v[u];
+        }
     }
     __syncthreads();
-    const int64_t per = ((len + kDetectThreads - 1) / kDetectThreads) | 1;
-    const int64_t i0 = min(len, tid * per), i1 = min(len, i0 + per);
+    const int per = ((len + kDetectThreads - 1) / kDetectThreads) | 1;
+    const int i0 = min(len, tid * per), i1 = min(len, i0 + per);
     int64_t local = 0, ymax = 0;
-    for (int64_t i = i0; i < i1; ++i) {
+    for (int i = i0; i < i1; ++i) {
         const int64_t y = P[i + 1];
         local += y;
         ymax = max(ymax, y < 0 ? -y : y);
@@ -530,7 +560,7 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
     if (lane == 0) warp_max[warp] = ymax;
     const int64_t off = block_exclusive_scan(local, warp_tot);   // (synchronises)
     int64_t run = off;
-    for (int64_t i = i0; i < i1; ++i) {
+    for (int i = i0; i < i1; ++i) {
         run += P[i + 1];
         P[i + 1] = run;
     }
@@ -555,15 +585,15 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
     // the block that holds start nwin - 1 reports the carry flags
     const bool carry_here = a.carry_out && a.nwin - 1 >= t0 && a.nwin - 1 < t0 + kDetectTile;
     for (int k = 0; k < a.nw; ++k) {
-        const int64_t thr_k = a.tint[(int64_t)trial * a.nw + k];
+        const int64_t thr_k = thr_s[k];
         if (thr_k == kNever) {
             if (carry_here && tid == 0) a.carry_out[(int64_t)trial * a.nw + k] = 0;
             continue;
         }
         // a run at start 0 continues one the previous gulp already reported
         const bool cin = a.carry_in && t0 == 0 && a.carry_in[(int64_t)trial * a.nw + k];
-        const int64_t W = a.widths[k];
-        const int Wi = (int)W;
+        const int Wi = width_s[k];
+        const int64_t W = Wi;
         const int64_t last = n - W;                     // last valid boxcar start
         const int64_t tend = min(t0 + kDetectTile, last + 1);
         auto box64 = [&](int64_t u) { return P[u - base + W] - P[u - base]; };
