@@ -1,19 +1,23 @@
 // dedisp.cu -- incoherent dedispersion on sm_103a (Section II-B, "Incoherent
 // Dedispersion"): D[d][t] = sum_c x[t + delay(c,d)][c], exact integers.
 //
-// Two kernels:
 //  * transpose_kernel: time-major uint8 [nsamps][nchans] -> channel-major
 //    [nchans][xt_pitch], zero padded, so that every channel row is a
 //    contiguous byte stream a bulk copy can stage.
-//  * dedisp_kernel: one block per (DM tile, time tile).  Channel rows are
-//    staged into shared memory with cp.async.bulk (TMA, completion on an
-//    mbarrier, two stages in flight).  Three byte-shifted copies of each row
-//    are built so that every (trial, channel) read is an aligned 32-bit word
-//    holding four consecutive samples.  Bytes are split into two 16-bit lanes
-//    (PRMT) and summed SIMD-within-a-register; at most 256 channels are
-//    summed per stage, so a lane never exceeds 256 * 255 < 2^16, and the
-//    lanes are flushed into int32 sums after every stage.  No tensor cores:
-//    the sum is not a dense contraction.
+//  * The sums: one block per (DM tile, time tile); channel rows are staged in
+//    shared memory with cp.async.bulk (TMA, completion on an mbarrier); bytes
+//    are summed in two 16-bit lanes per 32-bit word (SIMD within a register);
+//    at most 256 channels go into a lane before it is flushed into the int32
+//    sums, so a lane never exceeds 256 * 255 < 2^16.  Three shared-memory
+//    layouts, selected by the tile shape (kDedispConfigs):
+//      layout 0 -- three byte-shifted copies of each row, so every read is an
+//        aligned word (dedisp_kernel; dedisp_ws_kernel with producer warps);
+//      layout 1 -- rows widened to 16-bit samples (dedisp16_kernel);
+//      layout 2 -- byte rows only, aligned in registers by PRMT, a ring of
+//        stage buffers fed by one producer warp (dedisp_rows_kernel, the
+//        default shapes; its SEG instance writes per-segment partial sums for
+//        the sub-band variant's first stage).
+//    No tensor cores: the sum is not a dense contraction.
 #include <cstring>
 
 #include "common.cuh"
