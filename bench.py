@@ -37,12 +37,12 @@ METRIC = "DM-trial·samples/s"
 # capture of the full-size bench command (profiles/dedisp_rows_kernel_fast_4096ch.md).
 # Keyed by the kernel source it was measured on; a changed kernel, another workload or
 # another configuration reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "a76a4c06c1013bf3", "bytes": 37.88e9 + 5.74e9,
+DEDISP_TRAFFIC = {"source_sha256_16": "9e5e324f726ed58f", "bytes": 37.47e9 + 5.74e9,
                   "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22}
 # The same for the two stages of the sub-band variant (64-channel sub-bands, groups
 # of 8 trials): DRAM bytes of one step (4 launches of each stage), measured per launch
 # (profiles/subband_fast_4096ch.md), keyed by both kernel sources.
-SUBBAND_TRAFFIC = {"source_sha256_16": "a76a4c06c1013bf3+6752b94441917dc0",
+SUBBAND_TRAFFIC = {"source_sha256_16": "9e5e324f726ed58f+6752b94441917dc0",
                    "stage1": 31.98e9 + 46.35e9, "stage2": 46.04e9 + 5.67e9,
                    "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22, "S": 64, "G": 8}
 

@@ -56,54 +56,67 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
 
 namespace {
 
-constexpr int kTT = 64;
+constexpr int kTC = 64;    // channels per transpose tile
+constexpr int kTS = 256;   // samples per transpose tile (4 rows of 64 per thread)
 
-// One 64 x 64 byte tile of the transpose: rows t0.., channels c0.. of x
+// One 256 x 64 byte tile of the transpose: rows t0.., channels c0.. of x
 // [nsamps][nch] -> xt [nch][pitch] (zero beyond nsamps).  With ring_len > 0
 // row t is absolute sample a0 + t of a ring of ring_slots slots of ring_len
-// rows (a streamed beam's recent gulps).
+// rows (a streamed beam's recent gulps).  Each thread has four 16-byte loads
+// in flight and writes four 16-byte pieces of one channel row.
 __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, int64_t nsamps,
                                                int nch, int vec, uint8_t* __restrict__ xt,
                                                int64_t pitch, int64_t t0, int c0,
                                                int64_t ring_len = 0, int64_t a0 = 0,
                                                int ring_slots = 1) {
-    __shared__ __align__(16) uint8_t tile[kTT][kTT + 16];
+    __shared__ __align__(16) uint8_t tile[kTS][kTC + 16];
     const int tid = threadIdx.x;
+    const int seg = tid & 3;
     {
-        const int row = tid >> 2, seg = tid & 3;
-        const int64_t t = t0 + row;
-        const int c = c0 + seg * 16;
-        uint4 q = make_uint4(0, 0, 0, 0);
-        if (t < nsamps) {
-            int64_t r = t;
-            if (ring_len > 0) {
-                const int64_t a = a0 + t;
-                r = (a / ring_len) % ring_slots * ring_len + a % ring_len;
-            }
-            const uint8_t* xr = x + r * nch;
-            if (vec && c + 16 <= nch) {
-                q = __ldg(reinterpret_cast<const uint4*>(xr + c));
-            } else {
-                uint8_t v[16];
+        uint4 q[kTS / 64];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = (c + i < nch) ? xr[c + i] : 0;
-                memcpy(&q, v, 16);
+        for (int r = 0; r < kTS / 64; ++r) {
+            const int row = (tid >> 2) + 64 * r;
+            const int64_t t = t0 + row;
+            const int c = c0 + seg * 16;
+            q[r] = make_uint4(0, 0, 0, 0);
+            if (t < nsamps) {
+                int64_t rr = t;
+                if (ring_len > 0) {
+                    const int64_t a = a0 + t;
+                    rr = (a / ring_len) % ring_slots * ring_len + a % ring_len;
+                }
+                const uint8_t* xr = x + rr * nch;
+                if (vec && c + 16 <= nch) {
+                    q[r] = __ldg(reinterpret_cast<const uint4*>(xr + c));
+                } else {
+                    uint8_t v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = (c + i < nch) ? xr[c + i] : 0;
+                    memcpy(&q[r], v, 16);
+                }
             }
         }
-        *reinterpret_cast<uint4*>(&tile[row][seg * 16]) = q;
+#pragma unroll
+        for (int r = 0; r < kTS / 64; ++r)
+            *reinterpret_cast<uint4*>(&tile[(tid >> 2) + 64 * r][seg * 16]) = q[r];
     }
     __syncthreads();
     {
-        const int cr = tid >> 2, seg = tid & 3;
+        const int cr = tid >> 2;
         const int c = c0 + cr;
-        const int64_t t = t0 + seg * 16;
-        if (c < nch && t < pitch) {
-            uint8_t v[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = tile[seg * 16 + i][cr];
-            uint4 q;
-            memcpy(&q, v, 16);
-            *reinterpret_cast<uint4*>(xt + (int64_t)c * pitch + t) = q;
+        for (int r = 0; r < kTS / 64; ++r) {
+            const int row0 = (4 * r + seg) * 16;
+            const int64_t t = t0 + row0;
+            if (c < nch && t < pitch) {
+                uint8_t v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = tile[row0 + i][cr];
+                uint4 q;
+                memcpy(&q, v, 16);
+                *reinterpret_cast<uint4*>(xt + (int64_t)c * pitch + t) = q;
+            }
         }
     }
 }
@@ -111,7 +124,7 @@ __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, in
 __global__ void __launch_bounds__(256) transpose_kernel(const uint8_t* __restrict__ x,
                                                         int64_t nsamps, int nch, int vec,
                                                         uint8_t* __restrict__ xt, int64_t pitch) {
-    transpose_tile(x, nsamps, nch, vec, xt, pitch, (int64_t)blockIdx.x * kTT, blockIdx.y * kTT);
+    transpose_tile(x, nsamps, nch, vec, xt, pitch, (int64_t)blockIdx.x * kTS, blockIdx.y * kTC);
 }
 
 // Every file of a batch in one launch: block b handles tile b - prefix[j] of file j.
@@ -123,7 +136,7 @@ __global__ void __launch_bounds__(256) transpose_batch_kernel(const __grid_const
     const int64_t item = blk - tb.prefix[j];
     const int64_t tt = item % J.ttiles;
     const int ct = (int)(item / J.ttiles);
-    transpose_tile(J.x, J.nsamps, J.nch, J.vec, J.xt, J.pitch, tt * kTT, ct * kTT, J.ring_len,
+    transpose_tile(J.x, J.nsamps, J.nch, J.vec, J.xt, J.pitch, tt * kTS, ct * kTC, J.ring_len,
                    J.a0, J.ring_slots);
 }
 
@@ -1082,7 +1095,7 @@ cudaError_t run_dedisp(const DedispBatch& b, int stage_bytes, int* status, uint6
 cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
                              int64_t xt_pitch, cudaStream_t s) {
     const int vec = ((nchans & 15) == 0) && (((uintptr_t)x & 15u) == 0);
-    dim3 grid((unsigned)((xt_pitch + kTT - 1) / kTT), (unsigned)((nchans + kTT - 1) / kTT));
+    dim3 grid((unsigned)((xt_pitch + kTS - 1) / kTS), (unsigned)((nchans + kTC - 1) / kTC));
     transpose_kernel<<<grid, 256, 0, s>>>(x, nsamps, nchans, vec, xt, xt_pitch);
     return cudaGetLastError();
 }
@@ -1100,8 +1113,8 @@ TransposeJob make_transpose_job(const uint8_t* x, int64_t nsamps, int nchans, ui
     J.vec = ((nchans & 15) == 0) && (((uintptr_t)x & 15u) == 0);
     J.xt = xt;
     J.pitch = xt_pitch;
-    J.ttiles = (xt_pitch + kTT - 1) / kTT;
-    J.ctiles = (nchans + kTT - 1) / kTT;
+    J.ttiles = (xt_pitch + kTS - 1) / kTS;
+    J.ctiles = (nchans + kTC - 1) / kTC;
     return J;
 }
 

@@ -131,7 +131,7 @@ struct TransposeJob {
     int32_t nch, vec;
     uint8_t* xt;
     int64_t pitch;
-    int64_t ttiles;            // 64-sample tiles along time (of the padded pitch)
+    int64_t ttiles;            // 256-sample tiles along time (of the padded pitch)
     int32_t ctiles, pad_;      // 64-channel tiles
 };
 struct TransposeBatch {
