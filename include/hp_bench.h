@@ -36,6 +36,20 @@ int hp_measure_peaks(hp_peaks* out);
  * HP_ERR_INVALID_ARG for an unknown config. */
 int hp_dedisp_config(int config, int32_t out[8]);
 
+/* Self-test of the bounded device waits that every staged kernel uses (its
+ * barrier waits give up after HP_PARAM_TIMEOUT_S and latch HP_ERR_TIMEOUT, so
+ * a stalled copy ends the launch with a status instead of a hang).  One block
+ * of two warps on the current device: barrier A is initialised for one arrival
+ * that nobody makes; warp 0 waits on it (the wait runs out after limit_ns,
+ * latches HP_ERR_TIMEOUT and raises the block's abort flag) and warp 1 waits
+ * on it too (it leaves on that flag, or runs out itself).  Barrier B gets its
+ * one arrival and its wait must succeed.  Synchronous.  out (host memory):
+ * out[0] = the latched status (HP_ERR_TIMEOUT expected), out[1] = 1 if warp
+ * 0's wait ran out, out[2] = 1 if warp 1's wait gave up, out[3] = 1 if the
+ * wait on the completed barrier succeeded.  Returns HP_OK, HP_ERR_INVALID_ARG
+ * (null out, limit_ns outside (0, 10 s]) or HP_ERR_CUDA. */
+int hp_selftest_bounded_wait(int64_t limit_ns, int32_t out[4]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -497,6 +497,14 @@ def hp_dedisp_config(config: int) -> dict:
     return dict(zip(keys, (int(v) for v in out)))
 
 
+def hp_selftest_bounded_wait(limit_ns: int) -> dict:
+    """Run the bounded-wait self-test on the current GPU (synchronous)."""
+    out = (C.c_int32 * 4)()
+    check(lib().hp_selftest_bounded_wait(int(limit_ns), out), "hp_selftest_bounded_wait")
+    return {"status": int(out[0]), "warp0_ran_out": bool(out[1]), "warp1_gave_up": bool(out[2]),
+            "completed_wait_ok": bool(out[3])}
+
+
 def hp_measure_peaks() -> dict:
     """Integer-add, byte-permute and shared-memory load rates of the current GPU."""
     pk = Peaks()

@@ -53,11 +53,12 @@ CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("width_idx", "<i4"), ("sample", "<i8"
 RAW_DTYPE = np.dtype([("dm_idx", "<i4"), ("width_idx", "<i4"), ("sample", "<i8"), ("S", "<i8")])
 assert CAND_DTYPE.itemsize == 48 and RAW_DTYPE.itemsize == 24
 
-#: every symbol include/hp.h declares
+#: every symbol include/hp.h and include/hp_bench.h declare
 EXPORTS = ("hp_status_str", "hp_plan_create", "hp_plan_destroy", "hp_plan_set_param",
            "hp_plan_get_param", "hp_plan_delays", "hp_plan_max_delay", "hp_plan_workspace_bytes",
            "hp_plan_bind_workspace", "hp_search", "hp_dedisperse", "hp_detect", "hp_merge",
-           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks", "hp_dedisp_config", "hp_merge_static",
+           "hp_plan_sync_status", "hp_plan_stats", "hp_measure_peaks", "hp_dedisp_config",
+           "hp_selftest_bounded_wait", "hp_merge_static",
            "hp_plan_autotune", "hp_batch_create", "hp_batch_destroy", "hp_batch_set_config",
            "hp_batch_autotune", "hp_batch_search", "hp_batch_sync_status",
            "hp_batch_kernels_per_call", "hp_stream_open", "hp_stream_push", "hp_stream_end_beam",
@@ -146,6 +147,7 @@ def lib() -> C.CDLL:
             L.hp_plan_stats.argtypes = [vp, C.POINTER(Stats), i32]
             L.hp_measure_peaks.argtypes = [C.POINTER(Peaks)]
             L.hp_dedisp_config.argtypes = [C.c_int, C.c_void_p]
+            L.hp_selftest_bounded_wait.argtypes = [C.c_int64, C.c_void_p]
             L.hp_merge_static.argtypes = [vp, vp, i64, vp, vp, i32, i32, i64, i32, vp,
                                           C.POINTER(CandBuf)]
             L.hp_plan_autotune.argtypes = [vp, vp, i64, vp, C.POINTER(i32), C.POINTER(C.c_float)]

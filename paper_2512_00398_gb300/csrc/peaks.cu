@@ -98,8 +98,54 @@ double best_ms(K kernel, int blocks, uint32_t* out) {
     return best;
 }
 
+// The bounded waits of the staged kernels, exercised on barriers whose state
+// is known: A never completes (one expected arrival, none made), B completes
+// (its one arrival is made before anyone waits).  flags: status, warp 0 ran
+// out on A, warp 1 gave up on A, B's wait succeeded.
+__global__ void bounded_wait_kernel(uint64_t limit_ns, int* flags) {
+    __shared__ uint64_t bars[2];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) mbar_arrive(&bars[1]);
+    __syncthreads();
+    volatile int* abort = &abort_flag;
+    const bool b_done = mbar_wait_bounded(&bars[1], 0, limit_ns);
+    const bool a_done = mbar_wait_or_abort(&bars[0], 0, limit_ns, abort);
+    if (!a_done) latch_status(flags, HP_ERR_TIMEOUT);
+    if (lane == 0) {
+        if (warp == 0 && !a_done) atomicExch(&flags[1], 1);
+        if (warp == 1 && !a_done) atomicExch(&flags[2], 1);
+    }
+    if (tid == 0 && b_done) atomicExch(&flags[3], 1);
+}
+
 }  // namespace
 }  // namespace hp
+
+extern "C" int hp_selftest_bounded_wait(int64_t limit_ns, int32_t out[4]) {
+    if (!out || limit_ns <= 0 || limit_ns > 10000000000LL) return HP_ERR_INVALID_ARG;
+    int* d = nullptr;
+    if (cudaMalloc(&d, 4 * sizeof(int)) != cudaSuccess) return HP_ERR_CUDA;
+    int h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        hp::bounded_wait_kernel<<<1, 64>>>((uint64_t)limit_ns, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return HP_ERR_CUDA;
+    for (int i = 0; i < 4; ++i) out[i] = h[i];
+    return HP_OK;
+}
 
 extern "C" int hp_dedisp_config(int config, int32_t out[8]) {
     if (!out || config < 0 || config >= hp::kNumDedispConfigs) return HP_ERR_INVALID_ARG;

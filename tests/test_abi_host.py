@@ -261,3 +261,13 @@ def test_decimate_param():
         for bad in (-1, 2.5, 2):          # 4096 / 2 > 1024 blocks per sample
             with pytest.raises(hp.HPError):
                 p.set_param("decimate", bad)
+
+
+def test_selftest_bounded_wait_arguments():
+    lib = hp.lib()
+    import ctypes as C
+    out = (C.c_int32 * 4)()
+    assert lib.hp_selftest_bounded_wait(0, out) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_selftest_bounded_wait(-5, out) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_selftest_bounded_wait(20_000_000_000, out) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_selftest_bounded_wait(1000, None) == hp.HP_ERR_INVALID_ARG
