@@ -67,3 +67,34 @@ def test_reference_arm_other_ranks_exit_without_work():
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def _worker_one_fails(rank, world, port, out):
+    import datetime
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)                  # this rank dies between steps, before the timing exchange
+    try:
+        bench.max_over_ranks([1.0], dist, "cpu")
+        out.put((rank, "no error"))
+    except Exception as e:           # the survivor learns of it on the host
+        out.put((rank, type(e).__name__))
+
+
+def test_a_failed_rank_ends_the_survivors_exchange_with_an_error():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    procs = [mp.Process(target=_worker_one_fails, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, what = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and what != "no error"
+    assert procs[1].exitcode == 3
