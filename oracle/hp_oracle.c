@@ -32,6 +32,11 @@
  *                                 rectangular pulse S/N by hand
  *   decimated boxcars     pinned: numpy brute force on the scrunched series, R >= Wmax
  *                                 reduction to every start
+ *   hpo_detect_window     pinned: brute-force runs with window and carry, whole-series
+ *                                 window = plain detection, carry chains across gulps
+ *   hpo_rfi_clean         pinned: an independent numpy formulation on small inputs,
+ *                                 planted tones and spikes found exactly, clean noise and
+ *                                 dispersed pulses left alone
  */
 #include <math.h>
 #include <stdint.h>
