@@ -40,7 +40,7 @@ def test_two_ranks_max_and_weak_scaling_workloads():
     mp = torch.multiprocessing.get_context("spawn")
     q = mp.Queue()
     port = _free_port()
-    procs = [mp.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [mp.Process(target=_worker, args=(r, 2, port, q), daemon=True) for r in range(2)]
     for p in procs:
         p.start()
     res = sorted(q.get(timeout=120) for _ in procs)
@@ -76,10 +76,11 @@ def _worker_one_fails(rank, world, port, out):
     import bench
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world, timeout=datetime.timedelta(seconds=10))
+    bench.max_over_ranks([1.0 + rank], dist, "cpu")      # step 1: both ranks
     if rank == 1:
-        os._exit(3)                  # this rank dies between steps, before the timing exchange
+        os._exit(3)                  # this rank dies between steps
     try:
-        bench.max_over_ranks([1.0], dist, "cpu")
+        bench.max_over_ranks([1.0], dist, "cpu")          # step 2: the survivor alone
         out.put((rank, "no error"))
     except Exception as e:           # the survivor learns of it on the host
         out.put((rank, type(e).__name__))
@@ -87,14 +88,23 @@ def _worker_one_fails(rank, world, port, out):
 
 def test_a_failed_rank_ends_the_survivors_exchange_with_an_error():
     torch = pytest.importorskip("torch")
+    import queue
     mp = torch.multiprocessing.get_context("spawn")
     q = mp.Queue()
     port = _free_port()
-    procs = [mp.Process(target=_worker_one_fails, args=(r, 2, port, q)) for r in range(2)]
+    procs = [mp.Process(target=_worker_one_fails, args=(r, 2, port, q), daemon=True)
+             for r in range(2)]
     for p in procs:
         p.start()
-    rank, what = q.get(timeout=120)
-    for p in procs:
-        p.join(timeout=60)
-    assert rank == 0 and what != "no error"
+    try:
+        rank, what = q.get(timeout=120)
+    except queue.Empty:
+        rank, what = None, "survivor never returned"
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():         # our own child: end it by its handle
+                p.kill()
+                p.join(timeout=30)
+    assert rank == 0 and what not in ("no error", "survivor never returned"), what
     assert procs[1].exitcode == 3
