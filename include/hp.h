@@ -121,7 +121,7 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_T_GAP 3          /* merge: max gap between boxcar windows, samples */
 #define HP_PARAM_W_TOL 4          /* merge: max |width index difference| (>= 0) */
 #define HP_PARAM_RAW_CAPACITY 5   /* raw-candidate scratch capacity (>= 1024) */
-#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 22 */
+#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 12 */
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
 #define HP_PARAM_RFI 9            /* 1 = RFI mitigation before dedispersion (default 0) */
@@ -141,8 +141,8 @@ int hp_plan_destroy(hp_plan* plan);
  * hp_plan_delays then returns (hp_plan_max_delay its maximum; nout = nsamps -
  * that maximum).  hp_search, hp_dedisperse, hp_plan_autotune, batches (the
  * variant's files through their own two stages; hp_batch_autotune refuses it)
- * and streams (per searched buffer) follow the variant (tile shapes 17, 21,
- * 22 and 24 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
+ * and streams (per searched buffer) follow the variant (tile shapes 7, 11,
+ * 12 and 14 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
  * delay of channel c per unit DM in samples. */
 #define HP_PARAM_SUBBAND_CHANS 12 /* S: channels per sub-band, 0 = direct dedispersion (default) */
 #define HP_PARAM_SUBBAND_GROUP 13 /* G: trials per group, 1..ndm (default 8) */
@@ -168,7 +168,7 @@ int hp_plan_destroy(hp_plan* plan);
  * streams refuse it. */
 #define HP_PARAM_DECIMATE 15      /* R: 0 = every start (default) */
 
-#define HP_NUM_DEDISP_CONFIGS 27
+#define HP_NUM_DEDISP_CONFIGS 17
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);
@@ -262,9 +262,9 @@ int hp_merge(hp_plan* plan, const hp_raw_cand* raw_dev, const int64_t* nraw_dev,
              int64_t raw_capacity, const double* sigma_dev, void* stream,
              hp_cand_buf* cand_out);
 
-/* Try every byte-row dedispersion tile shape (HP_PARAM_DEDISP_CONFIG values
- * 10..) on this input (transpose + dedispersion, two timed passes each after a
- * warm-up, events on `stream`, synchronising), keep the fastest in the
+/* Try every dedispersion tile shape (HP_PARAM_DEDISP_CONFIG values 0 ..
+ * HP_NUM_DEDISP_CONFIGS - 1) on this input (transpose + dedispersion, two timed
+ * passes each after a warm-up, events on `stream`, synchronising), keep the fastest in the
  * plan (HP_PARAM_DEDISP_CONFIG) and report it.  best_config / best_ms are
  * optional host outputs.  The tile shape is the only thing tuned; results do
  * not depend on it. */
@@ -291,9 +291,9 @@ int hp_batch_destroy(hp_batch* batch);
 /* Use tile configuration `config` for every file (drops a captured graph). */
 int hp_batch_set_config(hp_batch* batch, int config);
 
-/* Time every byte-row tile shape (the configurations that HP_PARAM_DEDISP_CONFIG
- * values 10.. select) on these inputs, one timed pass each after one warm-up
- * pass (synchronising), and keep the fastest for the batch and its plans.
+/* Time every dedispersion tile shape (the configurations that
+ * HP_PARAM_DEDISP_CONFIG selects) on these inputs, one timed pass each after
+ * one warm-up pass (synchronising), and keep the fastest for the batch and its plans.
  * Inputs as for hp_batch_search. */
 int hp_batch_autotune(hp_batch* batch, const uint8_t* const* filterbanks_dev,
                       const int64_t* nsamps, void* stream, int* best_config, float* best_ms);

@@ -29,11 +29,11 @@ int hp_measure_peaks(hp_peaks* out);
 
 /* The shape of dedispersion tile shape `config` (HP_PARAM_DEDISP_CONFIG), for
  * rooflines: out[0..7] = trials per warp, 4-sample words per lane, warps along
- * the trials, warps along time, shared-memory bytes per stage, producer warps,
- * layout (0 byte rows + shifted copies, 1 16-bit copies, 2 byte rows aligned in
- * registers), stage buffers.  A byte-row (layout 2) kernel loads words + 1
- * row words per lane, channel and trial.  out is host memory.  Returns HP_OK or
- * HP_ERR_INVALID_ARG for an unknown config. */
+ * the trials, warps along time (plus one producer warp), shared-memory bytes
+ * per stage buffer, stage buffers, channel-pair loop unroll, threads per
+ * block.  A lane loads words + 1 row words per channel and trial and spends
+ * two PRMTs per word (alignment, odd bytes).  out is host memory.  Returns
+ * HP_OK or HP_ERR_INVALID_ARG for an unknown config. */
 int hp_dedisp_config(int config, int32_t out[8]);
 
 /* Self-test of the bounded device waits that every staged kernel uses (its

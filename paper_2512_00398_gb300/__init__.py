@@ -493,7 +493,7 @@ def hp_dedisp_config(config: int) -> dict:
     """The shape of a dedispersion tile shape (no GPU needed)."""
     out = (C.c_int32 * 8)()
     check(lib().hp_dedisp_config(int(config), out), "hp_dedisp_config")
-    keys = ("RD", "NW", "WD", "WT", "stage_bytes", "producers", "layout", "stages")
+    keys = ("RD", "NW", "WD", "WT", "stage_bytes", "stages", "unroll", "threads")
     return dict(zip(keys, (int(v) for v in out)))
 
 

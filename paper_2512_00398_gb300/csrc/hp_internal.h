@@ -28,23 +28,19 @@ constexpr int kKeySampleShift = 5;
 constexpr int64_t kMaxSamples = (int64_t)1 << 38;
 
 // ------------------------------------------------------ dedispersion tiles
-// Thread tile: RD trials x NW words per thread; WD warps along the trial axis,
-// WT along time; 32*WD*WT threads.  Layout 0 keeps bytes in shared memory
-// (a word = 4 samples, split into 16-bit lanes when summed); layout 1 keeps
-// 16-bit samples (a word = 2 samples, summed as they are).
-constexpr int kDedispStages = 3;         // shared-memory ring of channel stages
+// Thread tile: RD trials x NW words (4 byte samples each) per lane; WD warps
+// along the trial axis, WT along time, plus one producer warp.
 struct DedispConfig {
     int RD, NW, WD, WT;
-    int stage_bytes;   // shared memory per stage buffer (kDedispStages per block)
-    int producers;     // 0: every warp stages and computes; > 0: producer warps
-    int layout;        // 0: byte rows + 3 byte-shifted copies; 1: 16-bit even/odd copies;
-                       // 2: byte rows only, aligned in registers (deep copy ring)
-    int stages;        // stage buffers (layout 2; the others use kDedispStages)
+    int stage_bytes;   // shared memory per stage buffer
+    int stages;        // stage buffers in the ring
+    int unroll;        // channel-pair loop unroll
     int BD() const { return WD * RD; }
-    int BT() const { return WT * NW * (layout == 1 ? 64 : 128); }
-    int threads() const { return 32 * WD * WT; }
+    int BT() const { return WT * NW * 128; }
+    int threads() const { return 32 * (WD * WT + 1); }
 };
-constexpr int kNumDedispConfigs = 27;
+constexpr int kNumDedispConfigs = 17;
+constexpr int kDefaultDedispConfig = 12;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
 
 // One staged channel row of a DM tile (16 bytes, copied into shared memory).

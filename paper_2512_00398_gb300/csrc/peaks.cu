@@ -150,7 +150,7 @@ extern "C" int hp_selftest_bounded_wait(int64_t limit_ns, int32_t out[4]) {
 extern "C" int hp_dedisp_config(int config, int32_t out[8]) {
     if (!out || config < 0 || config >= hp::kNumDedispConfigs) return HP_ERR_INVALID_ARG;
     const hp::DedispConfig& c = hp::kDedispConfigs[config];
-    const int32_t v[8] = {c.RD, c.NW, c.WD, c.WT, c.stage_bytes, c.producers, c.layout, c.stages};
+    const int32_t v[8] = {c.RD, c.NW, c.WD, c.WT, c.stage_bytes, c.stages, c.unroll, c.threads()};
     for (int i = 0; i < 8; ++i) out[i] = v[i];
     return HP_OK;
 }

@@ -102,58 +102,43 @@ void compute_delays(hp_plan* p) {
 
 // ------------------------------------------------------- dedispersion tiling
 // A DM tile holds up to BD consecutive trials.  For every channel the block
-// stages the input row window [t0 + base, t0 + base + 4*nwords + 16) where
-// base = delay(c, first trial) rounded down to 16 bytes; a trial j of the tile
-// then reads 4-byte words at byte offset rel = delay(c, j) - base, served from
-// one of four byte-shifted copies of the row (rel & 3) so every read is an
-// aligned word.  Channels are packed into stages that fit the stage buffer.
+// stages the input row window [t0 + base, t0 + base + 4*nwords) where base =
+// the channel's smallest delay over the tile rounded down to 16 bytes; trial j
+// of the tile reads the words from (rel >> 2), rel = delay(c, j) - base, and
+// aligns them to rel & 3 in registers.  Channels are packed into stages that
+// fit the stage buffer.
 struct RowGeom {
     int32_t base;
     uint32_t nwords, bbytes, smem;
 };
 
 // lo / hi: the smallest and largest delay of channel c over the tile's trials
-RowGeom row_geom_span(int32_t lo, int32_t hi, int BT, int layout) {
+RowGeom row_geom_span(int32_t lo, int32_t hi, int BT) {
     RowGeom g;
     g.base = lo & ~15;
     const uint32_t span = (uint32_t)(hi - g.base);
-    if (layout == 0) {
-        // words of 4 samples per copy, a multiple of 4 so copies stay 16-byte aligned
-        g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4), 4);
-        g.bbytes = 4 * g.nwords + 16;
-        g.smem = g.bbytes + 12 * g.nwords;
-    } else if (layout == 1) {
-        // words of 2 samples per 16-bit copy (even- and odd-aligned), a multiple
-        // of 8; the byte row holds samples 0 .. 2 nwords
-        g.nwords = (uint32_t)align_up((span >> 1) + (uint32_t)(BT / 2), 8);
-        g.bbytes = 2 * g.nwords + 16;
-        g.smem = g.bbytes + 8 * g.nwords;
-    } else {
-        // the byte row alone: a trial reads words (rel >> 2) .. (rel >> 2) + BT/4
-        // and aligns them in registers
-        g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4) + 1, 4);
-        g.bbytes = 4 * g.nwords;
-        g.smem = g.bbytes;
-    }
+    // a trial reads words (rel >> 2) .. (rel >> 2) + BT/4
+    g.nwords = (uint32_t)align_up((span >> 2) + (uint32_t)(BT / 4) + 1, 4);
+    g.bbytes = 4 * g.nwords;
+    g.smem = g.bbytes;
     return g;
 }
 
 // direct tables grow with the trial index, so the first and last trial bound a channel
-RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT, int layout) {
+RowGeom row_geom(const hp_plan* p, int d0, int nd, int c, int BT) {
     return row_geom_span(p->delays[(size_t)d0 * p->nchans + c],
-                         p->delays[(size_t)(d0 + nd - 1) * p->nchans + c], BT, layout);
+                         p->delays[(size_t)(d0 + nd - 1) * p->nchans + c], BT);
 }
 
-// Table entries per channel pair and trial: two 32-bit words (layouts 0, 1:
-// byte offsets) or four (layout 2: byte offsets and PRMT selectors).
-uint32_t stage_table_bytes(int nchan, int BD, int layout) {
-    const size_t per = layout == 2 ? 4 : 2;
-    return (uint32_t)((size_t)((nchan + 1) / 2) * BD * per * sizeof(uint32_t));
+// Table entries per channel pair and trial: four 32-bit words (byte offsets of
+// the first word read in each channel, the PRMT selectors that align them).
+uint32_t stage_table_bytes(int nchan, int BD) {
+    return (uint32_t)((size_t)((nchan + 1) / 2) * BD * 4 * sizeof(uint32_t));
 }
 
-uint32_t stage_header(int nchan, int BD, int layout) {
+uint32_t stage_header(int nchan, int BD) {
     return (uint32_t)(align_up((size_t)nchan * sizeof(ChanDesc), 16) +
-                      align_up(stage_table_bytes(nchan, BD, layout), 16));
+                      align_up(stage_table_bytes(nchan, BD), 16));
 }
 
 // Stages, channel descriptors and address tables of one DM tile of nd trials
@@ -174,8 +159,8 @@ int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg
             lo = std::min(lo, delay(j, c));
             hi = std::max(hi, delay(j, c));
         }
-        geo_all[c] = row_geom_span(lo, hi, BT, C.layout);
-        if (geo_all[c].smem + stage_header(1, BD, C.layout) > budget) return HP_ERR_INVALID_ARG;
+        geo_all[c] = row_geom_span(lo, hi, BT);
+        if (geo_all[c].smem + stage_header(1, BD) > budget) return HP_ERR_INVALID_ARG;
     }
     TileDesc td;
     td.d0 = d0;
@@ -191,7 +176,7 @@ int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg
             uint32_t rows = 0;
             while (c + n < c_end && n < kStageMaxChans) {
                 const RowGeom& g = geo_all[c + n];
-                if (stage_header(n + 1, BD, C.layout) + rows + g.smem > budget) break;
+                if (stage_header(n + 1, BD) + rows + g.smem > budget) break;
                 rows += g.smem;
                 ++n;
             }
@@ -200,10 +185,10 @@ int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg
             sd.nchan = (uint32_t)n;
             sd.addr_off = (uint32_t)align_up((size_t)n * sizeof(ChanDesc), 16);
             sd.addr_begin = (uint32_t)T->addr.size();
-            sd.addr_bytes = stage_table_bytes(n, BD, C.layout);
+            sd.addr_bytes = stage_table_bytes(n, BD);
             sd.seg_row = seg_row[sg];
             sd.seg_info = (seg_trim[sg] << 1) | (c + n == c_end ? 1u : 0u);
-            uint32_t off = stage_header(n, BD, C.layout);
+            uint32_t off = stage_header(n, BD);
             uint32_t tx = (uint32_t)(n * sizeof(ChanDesc)) + sd.addr_bytes;
             std::vector<uint32_t> word0(n);   // per channel: byte offset of row copy 0
             for (int i = 0; i < n; ++i) {
@@ -219,9 +204,9 @@ int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg
                 off += g.smem;
                 T->max_reach = std::max<int64_t>(T->max_reach, (int64_t)g.base + g.bbytes);
             }
-            // table [pair][BD][2]: the byte offset of the word trial j reads first
-            // in each channel of the pair (copy rel & 3, word rel >> 2); layout 2
-            // appends the two PRMT selectors that align the row to rel & 3
+            // table [pair][BD][4]: for each channel of the pair the byte offset of
+            // the word trial j reads first (rel >> 2), then the two PRMT selectors
+            // that take bytes rel & 3 .. 3 + (rel & 3) of each word pair
             for (int pr = 0; pr < (n + 1) / 2; ++pr) {
                 for (int j = 0; j < BD; ++j) {
                     uint32_t sel[2] = {0, 0};
@@ -231,27 +216,11 @@ int append_tile(const Delay& delay, int nd, int nch, const std::vector<int>& seg
                         const int jj = j < nd ? j : 0;
                         const RowGeom& g = geo_all[cc];
                         const int32_t rel = delay(jj, cc) - g.base;
-                        const uint32_t offV = word0[i] + g.bbytes;
-                        if (C.layout == 2) {
-                            // the row's word rel >> 2; bytes rel & 3 .. 3 + (rel & 3)
-                            // of each word pair are selected by one PRMT
-                            T->addr.push_back(word0[i] + 4 * ((uint32_t)rel >> 2));
-                            sel[e] = 0x3210u + 0x1111u * ((uint32_t)rel & 3u);
-                        } else if (C.layout == 0) {
-                            // byte copy rel & 3 (copy 0 is the row itself), word rel >> 2
-                            const uint32_t r = (uint32_t)rel & 3u;
-                            const uint32_t vb = r == 0 ? word0[i] : offV + (r - 1) * 4 * g.nwords;
-                            T->addr.push_back(vb + 4 * ((uint32_t)rel >> 2));
-                        } else {
-                            // 16-bit copy rel & 1 (even, odd), word rel >> 1
-                            const uint32_t vb = offV + ((uint32_t)rel & 1u) * 4 * g.nwords;
-                            T->addr.push_back(vb + 4 * ((uint32_t)rel >> 1));
-                        }
+                        T->addr.push_back(word0[i] + 4 * ((uint32_t)rel >> 2));
+                        sel[e] = 0x3210u + 0x1111u * ((uint32_t)rel & 3u);
                     }
-                    if (C.layout == 2) {
-                        T->addr.push_back(sel[0]);
-                        T->addr.push_back(sel[1]);
-                    }
+                    T->addr.push_back(sel[0]);
+                    T->addr.push_back(sel[1]);
                 }
             }
             if (off > budget) return HP_ERR_INVALID_ARG;
@@ -325,7 +294,7 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
         while (nd < BD && d0 + nd < ndm) {
             bool ok = true;
             for (int c = nch - 1; c >= 0 && ok; --c)
-                ok = row_geom(p, d0, nd + 1, c, BT, C.layout).smem + stage_header(1, BD, C.layout) <= budget;
+                ok = row_geom(p, d0, nd + 1, c, BT).smem + stage_header(1, BD) <= budget;
             if (!ok) break;
             ++nd;
         }
@@ -933,7 +902,7 @@ MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw
 
 // The autotuner's search space: the byte-row kernels (every earlier layout is
 // slower on every shape measured and stays selectable by hand).
-bool autotune_candidate(int c) { return kDedispConfigs[c].layout == 2; }
+bool autotune_candidate(int c) { return c >= 0 && c < kNumDedispConfigs; }
 
 // time one transpose + dedispersion of `p` on `s` with events (synchronising)
 int time_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, cudaStream_t s, int reps,
@@ -969,7 +938,7 @@ int time_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, cudaStream_t s, i
 // ================================================================ batching
 struct hp_batch {
     std::vector<hp_plan*> plans;
-    int cfg = 22;
+    int cfg = hp::kDefaultDedispConfig;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> done;
     cudaEvent_t fork = nullptr;

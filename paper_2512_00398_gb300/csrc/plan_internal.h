@@ -57,7 +57,7 @@ struct hp_plan {
     int64_t t_gap = 0;
     int w_tol = 0;
     int64_t raw_capacity = (int64_t)1 << 22;
-    int dedisp_cfg = 22;
+    int dedisp_cfg = hp::kDefaultDedispConfig;
     uint64_t timeout_ns = 1000000000ull;
 
     std::vector<int32_t> delays;   // [ndm][nchans]

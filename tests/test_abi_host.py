@@ -83,7 +83,7 @@ def test_params_roundtrip_and_validation():
     o = w.obs
     with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
         assert p.get_param("w_tol") == w.nw
-        assert p.get_param("dedisp_config") == 22
+        assert p.get_param("dedisp_config") == 12
         for name, val in [("baseline_mode", 1), ("baseline_s", 0.5), ("dm_tol", 3), ("t_gap", -2),
                           ("w_tol", 1), ("raw_capacity", 4096), ("dedisp_config", 3),
                           ("stage_timing", 1), ("timeout_s", 0.25)]:
@@ -237,11 +237,11 @@ def test_width_sigma_param_and_arguments():
 
 def test_dedisp_config_shapes():
     shapes = [hp.hp_dedisp_config(c) for c in range(hp.HP_NUM_DEDISP_CONFIGS)]
-    assert shapes[22] == {"RD": 2, "NW": 7, "WD": 12, "WT": 1, "stage_bytes": 54 * 1024,
-                          "producers": 1, "layout": 2, "stages": 4}
-    assert all(s["layout"] in (0, 1, 2) and s["RD"] >= 1 and s["NW"] >= 1 for s in shapes)
-    # byte-row kernels keep an odd word count per lane (conflict-free row loads)
-    assert all(s["NW"] % 2 == 1 for s in shapes if s["layout"] == 2)
+    assert shapes[12] == {"RD": 2, "NW": 7, "WD": 12, "WT": 1, "stage_bytes": 54 * 1024,
+                          "stages": 4, "unroll": 2, "threads": 32 * 13}
+    assert all(s["RD"] >= 1 and s["NW"] >= 1 and s["threads"] <= 1024 for s in shapes)
+    # an odd word count per lane keeps the row loads conflict-free
+    assert all(s["NW"] % 2 == 1 for s in shapes)
     for bad in (-1, hp.HP_NUM_DEDISP_CONFIGS):
         with pytest.raises(hp.HPError):
             hp.hp_dedisp_config(bad)

@@ -15,7 +15,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 SNR_TOL = 1e-4
-SEGMENTED = [17, 21, 22, 24]
+SEGMENTED = [7, 11, 12, 14]
 
 
 @pytest.fixture(scope="module")
