@@ -328,10 +328,14 @@ typedef struct {
     double stage_ms[HP_NUM_STAGES];      /* summed event time of the recorded launches */
     int64_t stage_calls[HP_NUM_STAGES];  /* launches whose events were summed */
     int64_t kernel_launches;             /* CUDA kernels launched by the library */
+    int64_t device_allocs;               /* device allocations the plan made since it was
+                                            created (its allocator or cudaMalloc); the
+                                            paper's Table II counts the same for Heimdall */
 } hp_stats;
 
 /* Synchronise on the recorded events, write the totals since the last reset
- * into *out (host), then reset them if `reset` is non-zero. */
+ * into *out (host), then reset them if `reset` is non-zero (device_allocs is
+ * never reset). */
 int hp_plan_stats(hp_plan* plan, hp_stats* out, int reset);
 
 /* Candidate merging that allocates nothing (the paper has no counterpart).
@@ -347,19 +351,30 @@ int hp_plan_stats(hp_plan* plan, hp_stats* out, int reset);
  *   raw_capacity        entries of raw_dev, at most HP_MERGE_STATIC_MAX_RAW;
  *                       larger values are rejected with HP_ERR_INVALID_ARG
  *   sigma_dev           device double [ndm], per-trial sigma (as hp_detect writes)
- *   boxcar_widths       host, nw strictly increasing widths (as in the plan)
- *   dm_tol, t_gap, w_tol  merge tolerances (HP_PARAM_DM_TOL/T_GAP/W_TOL)
+ *   boxcar_widths       host, nw (1..32) strictly increasing widths (as in the plan)
+ *   dm_tol, t_gap, w_tol  merge tolerances, within the bounds that
+ *                       HP_PARAM_DM_TOL / T_GAP / W_TOL accept (else HP_ERR_INVALID_ARG)
  *   cand_out            merged clusters (see hp_cand_buf)
+ *   status_dev          optional device int32, caller-owned: when the device count
+ *                       *nraw_dev exceeds raw_capacity, only the first raw_capacity
+ *                       entries (in buffer order, which for hp_detect output is
+ *                       arbitrary) are merged and HP_ERR_CAND_OVERFLOW is written
+ *                       here if it still holds HP_OK (0); the caller sets it to 0
+ *                       beforehand and reads it once the stream has completed.
+ *                       With NULL such a truncation is not reported.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array, and its contents persist
- * from call to call (every word the kernels read is rewritten first, so nothing
- * has to be cleared); calls whose work overlaps on the GPU, e.g. on two streams
- * at once, race on it and must be ordered by the caller. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not call
+ * this after resetting the device (cudaDeviceReset), which moves the array.
+ * All calls share the one array, and its contents persist from call to call
+ * (every word the kernels read is rewritten first, so nothing has to be
+ * cleared); calls whose work overlaps on the GPU, e.g. on two streams at once,
+ * race on it and must be ordered by the caller. */
 #define HP_MERGE_STATIC_MAX_RAW 65536
 int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_dev, int64_t raw_capacity,
                     const double* sigma_dev, const int* boxcar_widths, int nw, int dm_tol,
-                    int64_t t_gap, int w_tol, void* stream, hp_cand_buf* cand_out);
+                    int64_t t_gap, int w_tol, void* stream, hp_cand_buf* cand_out,
+                    int32_t* status_dev);
 
 /* Device memory of the plan (its tables and, unless a workspace is bound, its
  * search workspace) from a caller's allocator instead of cudaMalloc/cudaFree,
@@ -440,6 +455,7 @@ typedef struct {
     int64_t device_bytes;    /* bytes allocated by the stream */
     int64_t tail_samples;    /* H */
     int64_t max_batch_seen;
+    int64_t device_allocs;   /* device allocations made since hp_stream_open (all at open) */
 } hp_stream_stats;
 
 /* Open a stream.  The plan (caller-owned, not used by the stream afterwards)

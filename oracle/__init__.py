@@ -93,6 +93,7 @@ def lib():
             L.hpo_detect_trial.argtypes = [vp, C.c_int64, C.c_int, C.c_double, vp, C.c_int,
                                            C.c_float, vp, C.c_int64, vp]
             L.hpo_sort_raw.argtypes = [vp, C.c_int64]
+            L.hpo_raw_snr.argtypes = [vp, C.c_int64, vp, vp]
             L.hpo_merge.argtypes = [vp, C.c_int64, vp, C.c_int, C.c_int64, C.c_int, vp,
                                     C.c_int64, vp]
             L.hpo_baseline_window.argtypes = [C.c_double, C.c_double]
@@ -254,6 +255,24 @@ def detect_trial(y: np.ndarray, d: int, sigma: float, widths, thr: float,
 def sort_raw(c: np.ndarray) -> np.ndarray:
     c = np.ascontiguousarray(c, dtype=RAW_DTYPE).copy()
     lib().hpo_sort_raw(_ptr(c), int(c.size))
+    return c
+
+
+def raw_with_snr(raw, sigma, widths) -> np.ndarray:
+    """Raw candidates given as (dm_idx, width_idx, sample, S) with their S/N
+    filled in from the per-trial sigmas (step c5): snr = S / (sigma_d sqrt(W))."""
+    raw = np.asarray(raw)
+    c = np.zeros(raw.size, dtype=RAW_DTYPE)
+    for f in ("dm_idx", "width_idx", "sample", "S"):
+        c[f] = raw[f]
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    if c.size:
+        if c["dm_idx"].min() < 0 or c["dm_idx"].max() >= sg.size:
+            raise ValueError("dm_idx outside the sigma array")
+        if c["width_idx"].min() < 0 or c["width_idx"].max() >= w.size:
+            raise ValueError("width_idx outside the width list")
+    lib().hpo_raw_snr(_ptr(c), int(c.size), _ptr(sg), _ptr(w))
     return c
 
 

@@ -25,6 +25,8 @@
  *   hpo_mad               pinned: numpy sort median, Gaussian unit RMS
  *   hpo_detect_trial      pinned: naive window sums, rectangular pulse, brute-force runs
  *   hpo_merge             pinned: brute-force O(N^2) components, permutation invariance
+ *   hpo_raw_snr           pinned: reproduces the S/N of every raw candidate a search
+ *                                 found, hand-worked values
  *   hpo_subband_delays    pinned: two-stage brute force, S = 1 / G = 1 / S = nchans
  *                                 reductions, closed-form error bound
  *   hpo_width_sigma       pinned: numpy brute force, W = 1 reduction to the MAD,
@@ -439,6 +441,17 @@ static int detect_into(const int64_t* y, int64_t n, int d, double sigma,
     }
     free(P);
     return 0;
+}
+
+/* S/N of raw candidates (step c5, the paper's reading: one sigma per trial,
+ * scaled by sqrt(W)) from their exact sums and the per-trial sigmas: the same
+ * FP64 expression as detect_into, snr = S / (sigma_d * sqrt(W)).  Used to
+ * merge raw candidates that come with sums and sigmas only. */
+void hpo_raw_snr(hpo_raw* c, int64_t n, const double* sigma, const int32_t* widths) {
+    for (int64_t i = 0; i < n; ++i) {
+        double sw = sqrt((double)widths[c[i].width_idx]);
+        c[i].snr = (double)c[i].S / (sigma[c[i].dm_idx] * sw);
+    }
 }
 
 /* Detection on one baseline-subtracted series y (length n) of trial d. */

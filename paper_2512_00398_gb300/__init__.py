@@ -258,10 +258,12 @@ def hp_merge(plan: Plan, raw, raw_count, sigma, stream=None, out=None, capacity:
 
 
 def hp_merge_static(raw, raw_count, sigma, widths, dm_tol=1, t_gap=0, w_tol=None, stream=None,
-                    out=None, capacity: int = 1 << 16):
+                    out=None, capacity: int = 1 << 16, status=None):
     """Merge device raw candidates without any device allocation by the
     library (its scratch is a fixed array built into the library); for
-    callers that must not allocate.  Returns the device (data, count) pair."""
+    callers that must not allocate.  ``status``: optional device int32 tensor
+    (set to 0 by the caller) in which a raw count beyond the buffer is
+    reported.  Returns the device (data, count) pair."""
     data, count = out if out is not None else new_cand_buf(capacity, raw.device)
     cap = data.numel() // CAND_DTYPE.itemsize
     b = _buf(data, count, cap)
@@ -271,7 +273,9 @@ def hp_merge_static(raw, raw_count, sigma, widths, dm_tol=1, t_gap=0, w_tol=None
                                 int(raw_cap), C.c_void_p(sigma.data_ptr()),
                                 w.ctypes.data_as(C.c_void_p), int(w.size), int(dm_tol), int(t_gap),
                                 int(w.size if w_tol is None else w_tol), _stream_ptr(stream),
-                                C.byref(b)), "hp_merge_static")
+                                C.byref(b),
+                                C.c_void_p(status.data_ptr() if status is not None else None)),
+          "hp_merge_static")
     return data, count
 
 
@@ -486,7 +490,7 @@ def hp_plan_stats(plan: Plan, reset: bool = True) -> dict:
     check(lib().hp_plan_stats(plan.handle, C.byref(st), int(bool(reset))), "hp_plan_stats")
     return {"stage_ms": {n: st.stage_ms[i] for i, n in enumerate(STAGE_NAMES)},
             "stage_calls": {n: int(st.stage_calls[i]) for i, n in enumerate(STAGE_NAMES)},
-            "kernel_launches": int(st.kernel_launches)}
+            "kernel_launches": int(st.kernel_launches), "device_allocs": int(st.device_allocs)}
 
 
 def hp_dedisp_config(config: int) -> dict:

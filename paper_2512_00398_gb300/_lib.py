@@ -94,7 +94,7 @@ class Peaks(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("stage_ms", C.c_double * HP_NUM_STAGES), ("stage_calls", C.c_int64 * HP_NUM_STAGES),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("device_allocs", C.c_int64)]
 
 
 class StreamConfig(C.Structure):
@@ -113,7 +113,7 @@ class StreamStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("gulps", C.c_int64), ("beam_slots", C.c_int32),
                 ("max_batch", C.c_int32), ("admitted", C.c_int32), ("waiting", C.c_int32),
                 ("device_bytes", C.c_int64), ("tail_samples", C.c_int64),
-                ("max_batch_seen", C.c_int64)]
+                ("max_batch_seen", C.c_int64), ("device_allocs", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -149,7 +149,7 @@ def lib() -> C.CDLL:
             L.hp_dedisp_config.argtypes = [C.c_int, C.c_void_p]
             L.hp_selftest_bounded_wait.argtypes = [C.c_int64, C.c_void_p]
             L.hp_merge_static.argtypes = [vp, vp, i64, vp, vp, i32, i32, i64, i32, vp,
-                                          C.POINTER(CandBuf)]
+                                          C.POINTER(CandBuf), vp]
             L.hp_plan_autotune.argtypes = [vp, vp, i64, vp, C.POINTER(i32), C.POINTER(C.c_float)]
             L.hp_batch_create.argtypes = [C.POINTER(vp), vp, i32]
             L.hp_batch_destroy.argtypes = [vp]

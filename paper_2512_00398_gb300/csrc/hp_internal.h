@@ -26,6 +26,7 @@ constexpr int kSortChunk = 2048;         // keys sorted per block before merging
 constexpr int kKeyDmShift = 43;          // sort key: dm << 43 | sample << 5 | width
 constexpr int kKeySampleShift = 5;
 constexpr int64_t kMaxSamples = (int64_t)1 << 38;
+constexpr int64_t kMaxMergeGap = 1000000000000000LL;   // |t_gap| bound (1e15 samples)
 
 // ------------------------------------------------------ dedispersion tiles
 // Thread tile: RD trials x NW words (4 byte samples each) per lane; WD warps

@@ -8,7 +8,8 @@
 // their scratch lives in one file-scope device array of fixed size, reserved
 // when the library is loaded and held on every GPU that loads it until the
 // process exits.  The caller still provides the raw candidates, their count,
-// the per-trial sigmas and the output buffer.
+// the per-trial sigmas, the output buffer and, to learn of a raw count beyond
+// the buffer it passed, an optional device status word.
 #include <mutex>
 
 #include "../../include/hp.h"
@@ -55,7 +56,9 @@ __global__ void put_widths_kernel(WidthList wl, int nw, int32_t* dst) {
     if (threadIdx.x < (unsigned)nw) dst[threadIdx.x] = wl.w[threadIdx.x];
 }
 
-// Device address of g_merge_scratch per device, resolved once per device.
+// Device address of g_merge_scratch per device, resolved once per device (the
+// first call on it) and kept for the life of the process; a device reset
+// (cudaDeviceReset) reloads the module and would leave this address stale.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
@@ -80,13 +83,17 @@ int scratch_address(unsigned char** out) {
 extern "C" int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_dev,
                                int64_t raw_capacity, const double* sigma_dev,
                                const int* boxcar_widths, int nw, int dm_tol, int64_t t_gap,
-                               int w_tol, void* stream, hp_cand_buf* cand_out) {
+                               int w_tol, void* stream, hp_cand_buf* cand_out,
+                               int32_t* status_dev) {
     using namespace hp;
     if (!raw_dev || !nraw_dev || !sigma_dev || !boxcar_widths || !cand_out || !cand_out->data ||
         !cand_out->count || cand_out->capacity < 0)
         return HP_ERR_INVALID_ARG;
     if (raw_capacity < 0 || raw_capacity > kStaticMaxRaw) return HP_ERR_INVALID_ARG;
-    if (nw < 1 || nw > kMaxWidths || dm_tol < 0 || w_tol < 0) return HP_ERR_INVALID_ARG;
+    // the same bounds as the plan's merge parameters (HP_PARAM_DM_TOL, T_GAP, W_TOL)
+    if (nw < 1 || nw > kMaxWidths || dm_tol < 0 || dm_tol > kMaxDMs || w_tol < 0 ||
+        w_tol > kMaxWidths || t_gap > kMaxMergeGap || t_gap < -kMaxMergeGap)
+        return HP_ERR_INVALID_ARG;
     WidthList wl = {};
     int32_t wmax = 0;
     for (int k = 0; k < nw; ++k) {
@@ -135,7 +142,9 @@ extern "C" int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_d
     m.out = cand_out->data;
     m.out_cap = cand_out->capacity;
     m.out_count = cand_out->count;
-    m.status = nullptr;
+    // a raw count beyond raw_capacity merges the first raw_capacity entries and
+    // latches HP_ERR_CAND_OVERFLOW here (when the caller gave a status word)
+    m.status = status_dev;
     int64_t launches = 0;
     return launch_merge(m, s, &launches) == cudaSuccess ? HP_OK : HP_ERR_CUDA;
 }

@@ -47,9 +47,12 @@ int plan_alloc(hp_plan* p, size_t bytes, void** out) {
             return HP_ERR_INVALID_ARG;
         }
         *out = m;
+        ++p->device_allocs;
         return HP_OK;
     }
-    return check_cuda(cudaMalloc(out, bytes));
+    const int rc = check_cuda(cudaMalloc(out, bytes));
+    if (!rc) ++p->device_allocs;
+    return rc;
 }
 
 void plan_free(hp_plan* p, void* ptr, size_t bytes) {
@@ -1180,7 +1183,7 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
             p->dm_tol = (int)v;
             return HP_OK;
         case HP_PARAM_T_GAP:
-            if (std::fabs(v) > 1e15 || v != std::floor(v)) return HP_ERR_INVALID_ARG;
+            if (std::fabs(v) > (double)kMaxMergeGap || v != std::floor(v)) return HP_ERR_INVALID_ARG;
             p->t_gap = (int64_t)v;
             return HP_OK;
         case HP_PARAM_W_TOL:
@@ -1468,6 +1471,7 @@ int hp_plan_stats(hp_plan* p, hp_stats* out, int reset) {
         if (reset) p->ev_used[st] = 0;
     }
     out->kernel_launches = p->launches;
+    out->device_allocs = p->device_allocs;
     if (reset) p->launches = 0;
     return HP_OK;
 }

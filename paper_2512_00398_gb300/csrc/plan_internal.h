@@ -111,6 +111,7 @@ struct hp_plan {
     std::vector<cudaEvent_t> ev[HP_NUM_STAGES];   // pairs (begin, end)
     int ev_used[HP_NUM_STAGES] = {};
     int64_t launches = 0;
+    int64_t device_allocs = 0;     // successful device allocations since creation
 
     int ndm() const { return (int)dm_list.size(); }
     int nw() const { return (int)widths.size(); }

@@ -600,6 +600,7 @@ int hp_stream_get_stats(hp_stream* s, hp_stream_stats* out) {
     out->device_bytes = (int64_t)(s->arena_bytes + s->plan->tables_bytes);
     out->tail_samples = s->H;
     out->max_batch_seen = s->max_batch_seen;
+    out->device_allocs = (s->arena ? 1 : 0) + s->plan->device_allocs;
     return HP_OK;
 }
 

@@ -42,6 +42,10 @@ MUTANTS = {
     "merge_dm_tol": ("c[j].dm_idx <= c[i].dm_idx + dm_tol;", "c[j].dm_idx < c[i].dm_idx + dm_tol;"),
     "merge_rep_last_tie": ("if (c[i].snr > o->snr) {", "if (c[i].snr >= o->snr) {"),
     "merge_t_hi": ("if (e > o->t_hi) o->t_hi = e;", "if (c[i].sample > o->t_hi) o->t_hi = c[i].sample;"),
+    "raw_snr_no_sqrt": ("c[i].snr = (double)c[i].S / (sigma[c[i].dm_idx] * sw);",
+                        "c[i].snr = (double)c[i].S / sigma[c[i].dm_idx];"),
+    "raw_snr_wrong_trial": ("c[i].snr = (double)c[i].S / (sigma[c[i].dm_idx] * sw);",
+                            "c[i].snr = (double)c[i].S / (sigma[0] * sw);"),
     # streamed search (window rule, carry, time offset)
     "stream_window_inclusive": ("if (first >= nwin) break;", "if (first > nwin) break;"),
     "stream_no_carry": ("if (first == 0 && carry_in && carry_in[k]) continue;",

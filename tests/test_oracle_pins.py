@@ -375,6 +375,26 @@ def test_merge_permutation_invariant_and_touching_windows():
     assert len(oracle.merge(two, widths, 1, 1)) == 1
 
 
+def test_raw_snr_hand_values_and_search_consistency(tiny_workload):
+    """S/N of raw candidates from their sums: hand-worked values (sigma 2,
+    W 4: S 120 -> 30; sigma 0.5, W 1: S -3 -> -6; sigma 3, W 16: S 84 -> 7),
+    and on a whole search every raw candidate's S/N is reproduced from its S,
+    its trial's sigma and its width."""
+    widths = np.array([1, 4, 16], np.int32)
+    raw = np.zeros(3, oracle.RAW_DTYPE)
+    raw[0] = (0, 1, 5, 120, 0.0)
+    raw[1] = (1, 0, 9, -3, 0.0)
+    raw[2] = (2, 2, 0, 84, 0.0)
+    got = oracle.raw_with_snr(raw, np.array([2.0, 0.5, 3.0]), widths)
+    assert list(got["snr"]) == [30.0, -6.0, 7.0]
+    w, s = tiny_workload
+    o = w.obs
+    r = oracle.search(s.data, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    assert r.raw.size > 0
+    again = oracle.raw_with_snr(r.raw, r.sigma, w.widths)
+    assert np.array_equal(again["snr"], r.raw["snr"])
+
+
 # ------------------------------------------------------- whole-path pins
 
 from paper_2512_00398_gb300.workloads import recovered  # noqa: E402  (the recovery criterion)
