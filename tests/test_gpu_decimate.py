@@ -80,11 +80,20 @@ def test_detect_raw_exact_on_the_grid(hp, torch, tiny):
 
 
 def test_batch_and_refusals(hp, torch, tiny):
+    """A batched search with decimated boxcars equals the oracle's and the
+    plain per-file search; streams and a negative R are refused."""
     w, s, fb = tiny
+    o = w.obs
     want = hp.search(_plan(hp, w, decimate=8), fb)
+    ref = oracle.search(s.data, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                        decimate=8).clusters
     b = hp.Batch([_plan(hp, w, decimate=8)])
-    for _ in range(3):
-        assert np.array_equal(b.search([fb])[0], want)
+    for i in range(3):
+        got = b.search([fb])[0]
+        if i == 0:
+            assert len(ref) > 0
+            _same_clusters(got, ref)
+        assert np.array_equal(got, want)
     b.close()
     with pytest.raises(hp.HPError):
         hp.Stream(_plan(hp, w, decimate=8), nbeams=1, gulp=4096)

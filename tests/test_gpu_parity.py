@@ -237,6 +237,12 @@ def test_fast_full_size_sampled(hp, torch, fast_full):
     assert int(got["members"].sum()) == raw_g.size
     assert (got["dm_lo"] <= got["dm_idx"]).all() and (got["dm_idx"] <= got["dm_hi"]).all()
     assert (got["t_lo"] <= got["sample"]).all() and (got["sample"] < got["t_hi"]).all()
+    # the search's clusters are hp_merge's of the raw list hp_detect finds; hp_merge
+    # itself is compared with the oracle at this scale in tests/test_gpu_merge.py
+    raw_d, cnt_d, sig_d, _ = hp.hp_detect(p, D, nout)
+    data, count = hp.hp_merge(p, raw_d, cnt_d, sig_d)
+    assert hp.hp_plan_sync_status(p) == hp.HP_OK
+    assert np.array_equal(hp.cands_to_numpy(data, count), got)
 
 
 def test_stress_full_size_sampled(hp, torch):
@@ -315,22 +321,35 @@ def test_long_runs_and_tile_edges(hp, torch, mode):
 
 
 def _small_batch(nfiles=5):
+    """Files of 65 536-131 072 samples, DM 0-300: 1024 channels at 49.152 and
+    64 us, 2048 at 64 us, 4096 at 49.152 and 64 us (seeds 350..354)."""
     from paper_2512_00398_gb300 import workloads
-    return workloads.batch(nfiles=nfiles, len_lo=1 << 16, len_hi=1 << 17, dm_hi=300.0,
-                           trial_density=0.4, wmax=256)
+    return workloads.batch(nfiles=nfiles, seed0=350, len_lo=1 << 16, len_hi=1 << 17,
+                           dm_hi=300.0, trial_density=0.4, wmax=256)
+
+
+def _oracle_search(w, x, **kw):
+    o = w.obs
+    return oracle.search(x, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold, **kw)
 
 
 def test_batch_matches_per_file_search(hp, torch):
     """Uneven files (channels, lengths, sampling times) searched as one batch:
-    eager first call, captured graph, replays and after autotuning, each equal
-    to hp_search of that file alone."""
+    every file's clusters equal the oracle's search of that file (exact tuples
+    and member statistics, S/N within 1e-4) and, eager first call, captured
+    graph, replays and after autotuning, hp_search of that file alone."""
     files = _small_batch()
+    shapes = {(w.obs.nchans, round(w.obs.tsamp * 1e6, 3)) for w in files}
+    assert {(1024, 64.0), (4096, 49.152), (2048, 64.0)} <= shapes
     gens = [w.generate() for w in files]
     fbs = [torch.from_numpy(g.data).cuda() for g in gens]
     plans = [_plan(hp, w) for w in files]
     want = [hp.search(p, fb) for p, fb in zip(plans, fbs)]
     assert sum(len(x) for x in want) > 0
     b = hp.Batch(plans)
+    first = b.search(fbs)
+    for w, g, got in zip(files, gens, first):
+        _compare_clusters(got, _oracle_search(w, g.data).clusters, w.threshold)
     for _ in range(3):
         got = b.search(fbs)
         for g, w_ in zip(got, want):
@@ -377,16 +396,24 @@ def test_torch_caching_allocator(hp, torch, tiny):
 
 
 def test_batch_with_rfi_matches_per_file(hp, torch):
+    """A batch with RFI mitigation on, planted tones and spikes: each file
+    equals the oracle's search of the oracle-cleaned input and its plain
+    per-file search."""
     files = _small_batch(nfiles=3)
-    fbs = []
+    xs, fbs = [], []
     for w in files:
         x = w.generate().data.astype(np.int32)
         x[:, [1, 2]] += 50
         x[::5000, :] += 60
-        fbs.append(torch.from_numpy(np.clip(x, 0, 255).astype(np.uint8)).cuda())
+        xs.append(np.clip(x, 0, 255).astype(np.uint8))
+        fbs.append(torch.from_numpy(xs[-1]).cuda())
     plans = [_plan(hp, w, rfi=1) for w in files]
     want = [hp.search(p, fb) for p, fb in zip(plans, fbs)]
     b = hp.Batch(plans)
+    first = b.search(fbs)
+    for w, x, got in zip(files, xs, first):
+        cleaned = oracle.rfi_clean(x, w.obs.tsamp).cleaned
+        _compare_clusters(got, _oracle_search(w, cleaned).clusters, w.threshold)
     for _ in range(2):
         for g, w_ in zip(b.search(fbs), want):
             assert np.array_equal(g, w_)

@@ -113,9 +113,20 @@ def test_subband_in_a_batch_matches_per_file(hp, torch, tiny):
     batched launch, the sub-band file through its own two stages; each equal to
     its plain search (eager, captured, replayed); batch autotuning refuses it."""
     w, s, fb, tab = tiny
+    o = w.obs
     p_sb, p_d = _plan(hp, w, subband_chans=16, subband_group=4), _plan(hp, w)
     want = [hp.search(_plan(hp, w, subband_chans=16, subband_group=4), fb), hp.search(_plan(hp, w), fb)]
     b = hp.Batch([p_sb, p_d])
+    first = b.search([fb, fb])
+    for got, sb in zip(first, [(16, 4), None]):
+        ref = oracle.search(s.data, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths,
+                            w.threshold, subband=sb).clusters
+        key = lambda c: (int(c["dm_idx"]), int(c["sample"]), int(c["width_idx"]))
+        assert [key(c) for c in got] == [key(c) for c in ref] and len(ref) > 0
+        for a, c in zip(got, ref):
+            assert abs(float(a["snr"]) - float(c["snr"])) <= SNR_TOL
+            for f in ("members", "dm_lo", "dm_hi", "t_lo", "t_hi"):
+                assert int(a[f]) == int(c[f])
     for _ in range(3):
         got = b.search([fb, fb])
         for g, w_ in zip(got, want):

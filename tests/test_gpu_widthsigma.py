@@ -129,12 +129,24 @@ def test_median_beyond_the_first_pass(hp, torch):
 
 
 def test_batch_matches_per_file(hp, torch, tiny):
+    """A batched search with per-width sigmas equals the oracle's and the
+    plain per-file search (eager, captured, replayed)."""
     w, s, fb = tiny
+    o = w.obs
     p1, p2 = _plan(hp, w, width_sigma=1), _plan(hp, w, width_sigma=1)
     want = hp.search(p1, fb)
+    ref = oracle.search(s.data, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                        width_sigma=True).clusters
     b = hp.Batch([p2])
-    for _ in range(3):                       # eager, captured, replayed
+    for i in range(3):                       # eager, captured, replayed
         got = b.search([fb])
+        if i == 0:
+            k = lambda c: (int(c["dm_idx"]), int(c["sample"]), int(c["width_idx"]))
+            assert [k(c) for c in got[0]] == [k(c) for c in ref] and len(ref) > 0
+            for a, c in zip(got[0], ref):
+                assert abs(float(a["snr"]) - float(c["snr"])) <= SNR_TOL
+                for f in ("members", "dm_lo", "dm_hi", "t_lo", "t_hi"):
+                    assert int(a[f]) == int(c[f])
         assert np.array_equal(got[0], want)
     b.close()
 
