@@ -215,6 +215,11 @@ struct SearchArgs {
     int32_t* refine_bucket;    // [ndm]
     int64_t* refine_rank;      // [ndm]
     int64_t* mad;              // [ndm]
+    // [ndm] upper bound of max |y| per trial from its |y| histogram (-1: none
+    // known), or null; a trial with ybound * ybound_w < 2^31 - 1 has every
+    // boxcar sum in int32 (ybound_w = the widest boxcar of the series y)
+    int64_t* ybound;
+    int64_t ybound_w;
     double* sigma;             // [ndm]
     int64_t* tint;             // [ndm][nw] integer thresholds
     int32_t* Y;                // [ndm][ypitch] baseline-subtracted series y = D - b, written

@@ -472,6 +472,7 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
     L.rbucket = take((size_t)ndm * 4);
     L.rrank = take((size_t)ndm * 8);
     L.mad = take((size_t)ndm * 8);
+    L.ybound = take((size_t)ndm * 8);
     L.sigma = take((size_t)ndm * 8);
     L.tint = take((size_t)ndm * p->nw() * 8);
     if (p->decimate > 0) {
@@ -770,6 +771,8 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.refine_bucket = (int32_t*)(ws + L.rbucket);
     a.refine_rank = (int64_t*)(ws + L.rrank);
     a.mad = (int64_t*)(ws + L.mad);
+    a.ybound = (int64_t*)(ws + L.ybound);
+    a.ybound_w = p->wmax;
     a.sigma = (double*)(ws + L.sigma);
     a.tint = (int64_t*)(ws + L.tint);
     a.raw = raw;

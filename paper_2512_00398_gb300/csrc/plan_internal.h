@@ -19,7 +19,7 @@ struct Layout {
     int64_t xt_pitch = 0, dpitch = 0;
     int64_t lvl_pitch_a = 0, lvl_pitch_b = 0, mean_pitch = 0;
     size_t xt = 0, D = 0, lvl_a = 0, lvl_b = 0, mean = 0, hist = 0, rbucket = 0, rrank = 0,
-           mad = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
+           mad = 0, ybound = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
            vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
            dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
     // RFI stage: channel counts, statistics and flags, the zero-DM series and

@@ -344,10 +344,30 @@ __device__ void find_rank_bin(const uint32_t* __restrict__ hrow, int bins, int64
 __global__ void __launch_bounds__(1024) mad_select_kernel(uint32_t* __restrict__ hist, int64_t n,
                                                           int32_t* __restrict__ bucket,
                                                           int64_t* __restrict__ rank,
-                                                          int64_t* __restrict__ mad) {
+                                                          int64_t* __restrict__ mad,
+                                                          int64_t* __restrict__ ybound) {
     const int trial = blockIdx.x;
     uint32_t* hrow = hist + (int64_t)trial * kHistBins;
     const int64_t k = (n - 1) / 2;
+    if (ybound) {
+        // an upper bound of max |y| from the highest non-empty bin: exact below
+        // kHistFine, the top of a coarse bin above, none for the last coarse bin
+        __shared__ int s_top;
+        if (threadIdx.x == 0) s_top = -1;
+        __syncthreads();
+        int top = -1;
+        for (int b = threadIdx.x; b < kHistBins; b += blockDim.x)
+            if (hrow[b]) top = b;
+        if (top >= 0) atomicMax(&s_top, top);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int t = s_top;
+            ybound[trial] = t < 0 ? 0
+                          : t < kHistFine ? (int64_t)t
+                          : t == kHistBins - 1 ? -1
+                          : ((int64_t)(t - kHistFine + 1) << 12) - 1;
+        }
+    }
     int bin;
     int64_t before;
     find_rank_bin(hrow, kHistBins, k, &bin, &before);
@@ -429,6 +449,15 @@ __global__ void sigma_kernel(const int64_t* __restrict__ mad, int ndm,
 constexpr int kDetectThreads = 256;
 constexpr int kDetectPer = kDetectTile / kDetectThreads;   // starts per thread
 
+// Every boxcar sum of this trial fits int32: its |y| bound times the widest
+// boxcar of the series stays below 2^31 - 1.
+__device__ __forceinline__ bool narrow_trial(const SearchArgs& a, int trial) {
+    if (!a.ybound) return false;
+    const int64_t yb = a.ybound[trial];
+    return yb >= 0 && yb * a.ybound_w < (int64_t)INT32_MAX;
+}
+
+
 __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* warp_tot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t x = v;
@@ -508,16 +537,17 @@ __device__ __forceinline__ bool follow_run(int64_t ts, int64_t last, int64_t bas
     return tail;
 }
 
-__global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_constant__ SearchArgs a) {
+// One tile of starts of one trial with an int64 prefix (the trials that
+// detect32_kernel cannot take).
+__device__ void detect_tile(const SearchArgs& a, int trial, int64_t tile) {
     extern __shared__ int64_t P[];   // P[i] = sum of y over samples [base, base + i)
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t warp_max[32];
     __shared__ unsigned above_bits[kDetectThreads / 32][kDetectPer];
     __shared__ int64_t thr_s[kMaxWidths];     // this trial's integer thresholds
     __shared__ int32_t width_s[kMaxWidths];
-    const int trial = blockIdx.y;
     const int64_t n = a.nout;
-    const int64_t t0 = (int64_t)blockIdx.x * kDetectTile;
+    const int64_t t0 = tile * kDetectTile;
     const int64_t base = t0 - 1;
     const int len = (int)min((int64_t)kDetectTile + a.wmax, n - base);   // <= tile + kMaxWidth
     const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
@@ -677,6 +707,265 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
             }
         }
         __syncwarp();
+    }
+}
+
+// Blocks loop over the tiles of their trial, a few blocks per trial: the
+// trials this kernel takes are rare, and the others leave at once.
+constexpr int kDetectBlocksPerTrial = 8;
+__global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_constant__ SearchArgs a) {
+    const int trial = blockIdx.y;
+    if (narrow_trial(a, trial)) return;   // detect32_kernel takes the trial
+    const int64_t ntiles = (a.nout + kDetectTile - 1) / kDetectTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        detect_tile(a, trial, tile);
+        __syncthreads();   // the shared prefix and bit masks are rebuilt for the next tile
+    }
+}
+
+// ------------------------------------------------ detection, 32-bit prefix
+// For trials whose every boxcar sum fits int32 (ybound * widest boxcar <
+// 2^31 - 1): 512 threads, each testing 8 consecutive starts, a tile of 4096
+// starts per block.  The prefix of y over the tile, 8 samples before it and
+// the widest boxcar after it is kept as wrapping 32-bit sums in shared memory
+// (a difference of two is the exact boxcar sum), with the tile's first start
+// at an index that is a multiple of 8: for a width that is a multiple of 8 a
+// thread reads the 8 sums it needs with two 16-byte loads, widths below 8 come
+// from the thread's own registers, and each start costs one subtract and one
+// compare per width.  The hot loop only records which widths had a start above
+// threshold; the rare warps with one find the run starts and follow each run
+// (as detect_kernel), runs leaving the halo go to tail_kernel.
+constexpr int kD32Threads = 512;
+constexpr int kD32Per = 8;                          // consecutive starts per thread
+constexpr int kD32Tile = kD32Threads * kD32Per;     // starts per block
+constexpr int kD32Lead = 8;                         // prefix entries before the first start
+
+__device__ __forceinline__ uint32_t block_exclusive_scan32(uint32_t v, uint32_t* warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    return x - v + (warp > 0 ? warp_tot[warp - 1] : 0u);
+}
+
+// q[i] = the prefix W entries after p[i] for a width W below 8: from this
+// thread's own 8 entries p and the next 8, nx
+template <int W>
+__device__ __forceinline__ void shifted8(const uint32_t (&p)[8], const uint32_t (&nx)[8],
+                                         uint32_t (&q)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) q[i] = i + W < 8 ? p[i + W] : nx[i + W - 8];
+}
+
+__global__ void __launch_bounds__(kD32Threads) detect32_kernel(const __grid_constant__ SearchArgs a) {
+    extern __shared__ __align__(16) uint32_t A[];   // A[i] = sum of y over [base, base + i)
+    __shared__ uint32_t warp_tot[32];
+    __shared__ int32_t thr_s[kMaxWidths];           // INT32_MAX: this width finds nothing
+    __shared__ int32_t width_s[kMaxWidths];
+    const int trial = blockIdx.y;
+    if (!narrow_trial(a, trial)) return;             // detect_kernel takes the trial
+    const int64_t n = a.nout;
+    const int64_t t0 = (int64_t)blockIdx.x * kD32Tile;
+    const int64_t base = t0 - kD32Lead;
+    const int len = (int)min((int64_t)kD32Lead + kD32Tile + a.wmax, n - base);
+    const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < a.nw) {
+        const int64_t tk = a.tint[(int64_t)trial * a.nw + tid];
+        thr_s[tid] = (int32_t)min(tk, (int64_t)INT32_MAX);
+        width_s[tid] = a.widths[tid];
+    }
+    // the prefix: 8 consecutive samples per thread per pass, coalesced 16-byte
+    // loads where the row allows them; A[i] for i = 8 tid .. 8 tid + 7 holds the
+    // sum before sample base + i (entries past len repeat the total)
+    const bool vec = (a.ypitch & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0;
+    uint32_t carry = 0;
+    for (int p0 = 0; p0 < len; p0 += kD32Tile) {
+        const int i0 = p0 + kD32Per * tid;
+        const int64_t s0 = base + i0;
+        uint32_t v[8];
+        if (vec && s0 >= 0 && i0 + 8 <= len) {
+            const int4* q = reinterpret_cast<const int4*>(yrow + s0);
+            const int4 x = __ldg(q), y = __ldg(q + 1);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                v[e] = (i0 + e < len && s0 + e >= 0) ? (uint32_t)__ldg(yrow + s0 + e) : 0u;
+        }
+        uint32_t ex[8];
+        uint32_t run = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            ex[e] = run;
+            run += v[e];
+        }
+        const uint32_t off = carry + block_exclusive_scan32(run, warp_tot);   // (synchronises)
+        if (i0 <= len) {   // entries up to len + 7 (the allocation holds them)
+            *reinterpret_cast<uint4*>(&A[i0]) =
+                make_uint4(off + ex[0], off + ex[1], off + ex[2], off + ex[3]);
+            *reinterpret_cast<uint4*>(&A[i0 + 4]) =
+                make_uint4(off + ex[4], off + ex[5], off + ex[6], off + ex[7]);
+        }
+        carry += warp_tot[kD32Threads / 32 - 1];
+        __syncthreads();   // warp_tot is rewritten by the next pass
+    }
+    if (tid == 0) A[len] = carry;
+    __syncthreads();
+
+    const int kb = kD32Lead + kD32Per * tid;          // prefix index of start tb
+    const int64_t tb = t0 + kD32Per * tid;            // this thread's first start
+    uint32_t p[8], nx[8];
+    {
+        const uint4 a0 = *reinterpret_cast<const uint4*>(&A[kb]);
+        const uint4 a1 = *reinterpret_cast<const uint4*>(&A[kb + 4]);
+        const uint4 b0 = *reinterpret_cast<const uint4*>(&A[kb + 8]);
+        const uint4 b1 = *reinterpret_cast<const uint4*>(&A[kb + 12]);
+        p[0] = a0.x; p[1] = a0.y; p[2] = a0.z; p[3] = a0.w;
+        p[4] = a1.x; p[5] = a1.y; p[6] = a1.z; p[7] = a1.w;
+        nx[0] = b0.x; nx[1] = b0.y; nx[2] = b0.z; nx[3] = b0.w;
+        nx[4] = b1.x; nx[5] = b1.y; nx[6] = b1.z; nx[7] = b1.w;
+    }
+    // the prefix W entries after each of this thread's starts
+    auto ahead = [&](int W, uint32_t (&q)[8]) {
+        if ((W & 7) == 0) {
+            const uint4 c0 = *reinterpret_cast<const uint4*>(&A[kb + W]);
+            const uint4 c1 = *reinterpret_cast<const uint4*>(&A[kb + W + 4]);
+            q[0] = c0.x; q[1] = c0.y; q[2] = c0.z; q[3] = c0.w;
+            q[4] = c1.x; q[5] = c1.y; q[6] = c1.z; q[7] = c1.w;
+        } else if (W < 8) {
+            switch (W) {
+                case 1: shifted8<1>(p, nx, q); break;
+                case 2: shifted8<2>(p, nx, q); break;
+                case 3: shifted8<3>(p, nx, q); break;
+                case 4: shifted8<4>(p, nx, q); break;
+                case 5: shifted8<5>(p, nx, q); break;
+                case 6: shifted8<6>(p, nx, q); break;
+                default: shifted8<7>(p, nx, q); break;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = A[kb + W + i];
+        }
+    };
+    // hot loop: which widths have an above-threshold start among this thread's 8
+    uint32_t hit = 0;
+    for (int k = 0; k < a.nw; ++k) {
+        const int32_t thr = thr_s[k];
+        if (thr == INT32_MAX) continue;
+        const int W = width_s[k];
+        const int64_t lim = n - W - tb;               // starts tb + i, i <= lim, exist
+        uint32_t q[8];
+        ahead(W, q);
+        bool any = false;
+        if (lim >= 7) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) any |= (int32_t)(q[i] - p[i]) >= thr;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) any |= i <= lim && (int32_t)(q[i] - p[i]) >= thr;
+        }
+        if (any) hit |= 1u << k;
+    }
+
+    // the block that holds start nwin - 1 reports the carry flags
+    if (a.carry_out && tid == 0 && a.nwin - 1 >= t0 && a.nwin - 1 < t0 + kD32Tile) {
+        const int i = (int)(a.nwin - 1 - base);
+        for (int k = 0; k < a.nw; ++k) {
+            const int W = width_s[k];
+            const bool above = thr_s[k] != INT32_MAX && a.nwin - 1 <= n - W &&
+                               (int32_t)(A[i + W] - A[i]) >= thr_s[k];
+            a.carry_out[(int64_t)trial * a.nw + k] = above ? 1 : 0;
+        }
+    }
+
+    if (!__any_sync(0xffffffffu, hit != 0)) return;
+    // rare: run starts and runs of the widths some lane flagged
+    unsigned todo = __reduce_or_sync(0xffffffffu, hit);
+    const bool cin_any = a.carry_in && t0 == 0;
+    while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int32_t thr = thr_s[k];
+        const int W = width_s[k];
+        const int64_t last = n - W;
+        const int64_t lim = last - tb;
+        uint32_t q[8];
+        ahead(W, q);
+        unsigned above = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i <= lim && (int32_t)(q[i] - p[i]) >= thr) above |= 1u << i;
+        // a start opens a run when the start before it is below threshold; for
+        // this thread's first start that is the previous thread's last, or for
+        // the block's first start the start before the tile
+        const unsigned prev = __shfl_up_sync(0xffffffffu, above, 1);
+        bool left;
+        if (lane > 0) {
+            left = (prev >> 7) & 1u;
+        } else {
+            const int64_t tl = tb - 1;                // kb - 1 >= kD32Lead - 1 >= 0
+            left = tl >= 0 && tl <= last && (int32_t)(A[kb - 1 + W] - A[kb - 1]) >= thr;
+        }
+        unsigned starts = above & ~((above << 1) | (left ? 1u : 0u)) & 0xffu;
+        // streamed search: runs begin inside the window, and a run at start 0
+        // that the previous gulp left open is not reported again
+        if (a.nwin < tb + 8) starts &= a.nwin <= tb ? 0u : (1u << (int)(a.nwin - tb)) - 1u;
+        if (cin_any && tb == 0 && a.carry_in[(int64_t)trial * a.nw + k]) starts &= ~1u;
+        unsigned lanes = __ballot_sync(0xffffffffu, starts != 0);
+        auto box32 = [&](int64_t u) {
+            const int i = (int)(u - base);
+            return (int64_t)(int32_t)(A[i + W] - A[i]);
+        };
+        while (lanes) {
+            const int L = __ffs(lanes) - 1;
+            lanes &= lanes - 1;
+            unsigned sL = __shfl_sync(0xffffffffu, starts, L);
+            const int64_t tL = t0 + (int64_t)kD32Per * (warp * 32 + L);
+            while (sL) {
+                const int e = __ffs(sL) - 1;
+                sL &= sL - 1;
+                int64_t bS, bt, tu = 0;
+                const bool tail = follow_run(tL + e, last, base, len, (int64_t)W, (int64_t)thr,
+                                             box32, lane, &bS, &bt, &tu);
+                if (lane == 0) {
+                    if (!tail) {
+                        emit(a, trial, k, bt, bS);
+                    } else {
+                        const unsigned long long qi = atomicAdd(
+                            reinterpret_cast<unsigned long long*>(a.tail_count), 1ull);
+                        if ((int64_t)qi < a.tail_cap) {
+                            TailRec r;
+                            r.trial = trial;
+                            r.k = k;
+                            r.u = tu;
+                            r.S_prev = box32(tu - 1);
+                            r.best_S = bS;
+                            r.best_t = bt;
+                            a.tails[qi] = r;
+                        } else {
+                            latch_status(a.status, HP_ERR_CAND_OVERFLOW);
+                        }
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -1000,9 +1289,19 @@ cudaError_t launch_detect(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
     if ((e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
-    const dim3 dgrid((unsigned)ceil_div(a.nout, kDetectTile), a.ndm);
+    const dim3 dgrid((unsigned)std::min<int64_t>(ceil_div(a.nout, kDetectTile), kDetectBlocksPerTrial),
+                     a.ndm);
     ++*nlaunch;
     detect_kernel<<<dgrid, kDetectThreads, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the trials whose boxcar sums all fit int32 (nearly all)
+    const size_t smem32 = ((size_t)kD32Lead + kD32Tile + (size_t)a.wmax + 16) * sizeof(uint32_t);
+    if ((e = cudaFuncSetAttribute(detect32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem32)) != cudaSuccess)
+        return e;
+    const dim3 dgrid32((unsigned)ceil_div(a.nout, kD32Tile), a.ndm);
+    ++*nlaunch;
+    detect32_kernel<<<dgrid32, kD32Threads, smem32, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
     tail_kernel<<<64, 128, 0, s>>>(a);
@@ -1023,7 +1322,8 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
                                                 yvec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
-    mad_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, n, a.refine_bucket, a.refine_rank, a.mad);
+    mad_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, n, a.refine_bucket, a.refine_rank, a.mad,
+                                           a.ybound);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
     mad_refine_hist_kernel<<<hgrid, 256, 0, s>>>(a.Y, a.ypitch, n, yvec, a.refine_bucket, a.hist);

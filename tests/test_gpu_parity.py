@@ -108,6 +108,36 @@ def test_detect_exact_on_oracle_series(hp, torch, tiny):
         assert go[(int(r["dm_idx"]), int(r["sample"]), int(r["width_idx"]))] == int(r["S"])
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_detect_narrow_and_wide_trials(hp, torch, mode):
+    """Trials whose boxcar sums all fit int32 (the 32-bit detection) next to
+    trials with spikes of ~2^24 (|y| bound x widest boxcar >= 2^31: the int64
+    detection), in one call: MADs, sigmas and raw candidates exact against the
+    oracle.  Runs near tile edges, a pulse at the series end."""
+    rng = np.random.default_rng(41 + mode)
+    ndm, nout = 6, 50000
+    widths = np.array([1, 2, 3, 8, 12, 64, 256], np.int32)
+    D = rng.normal(0, 30, size=(ndm, nout)).round().astype(np.int64)
+    for d in range(ndm):
+        for t in rng.integers(0, nout - 300, 6):
+            D[d, t:t + int(rng.integers(1, 200))] += int(rng.integers(20, 80))
+        D[d, 4096 * 3 - 2:4096 * 3 + 3] += 400          # across a tile edge
+        D[d, -5:] += 300                                # up to the last start
+    D[4, rng.integers(0, nout, 40)] += 1 << 24           # wide trials
+    D[5, rng.integers(0, nout, 40)] -= 1 << 24
+    D = D.astype(np.int32)
+    raw_o, sig_o, mad_o = oracle.search_trials(D, 0, 1e-3, widths, 5.0, baseline_mode=mode,
+                                               baseline_s=0.5)
+    p = hp.Plan(16, 1500.0, -1.0, 1e-3, np.zeros(ndm, np.float32), widths, 5.0,
+                baseline_mode=mode, baseline_s=0.5)
+    raw_g, sig_g, mad_g = hp.detect(p, torch.from_numpy(D).cuda(), nout)
+    assert np.array_equal(mad_g, mad_o) and np.array_equal(sig_g, sig_o)
+    assert len(raw_o) > 0 and {4, 5} <= set(int(r["dm_idx"]) for r in raw_o)
+    go = sorted((int(r["dm_idx"]), int(r["sample"]), int(r["width_idx"]), int(r["S"])) for r in raw_g)
+    wo = sorted((int(r["dm_idx"]), int(r["sample"]), int(r["width_idx"]), int(r["S"])) for r in raw_o)
+    assert go == wo
+
+
 def test_search_matches_oracle_tiny(hp, torch, tiny):
     w, s, fb = tiny
     o = w.obs
