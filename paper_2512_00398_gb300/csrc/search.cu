@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(256) remedian_pass_kernel(const int32_t* __res
 
 // ------------------------------------------------------- baseline walkers
 // Exact baseline b(t) evaluated at consecutive samples t, t+1, ...
+
 struct MedianWalker {
     const int32_t* m;
     int64_t M, P, half;
@@ -260,45 +261,76 @@ __device__ __forceinline__ void load_chunk32(const int32_t* __restrict__ row, in
 }
 
 // Histogram of |y| per trial; also writes y = D - b (int32: |D|, |b| < 2^21)
-// for the passes after it.  Each thread reads its whole chunk before it
-// writes, so Y may alias D (median mode, whose walker reads only the knots).
+// for the passes after it.  A block takes kHistBlock consecutive samples of
+// one trial; each thread walks kHistSpan consecutive samples with one baseline
+// walker (set up once, its divisions amortised over the span), kHistStep at a
+// time: every byte it loads is used, and the block's shared bins are cleared
+// and flushed once per kHistBlock samples.  Each thread reads a step before it
+// writes it, so Y may alias D (median mode, whose walker reads only the knots).
+constexpr int kHistThreads = 256;
+constexpr int kHistSpan = 256;                           // samples per thread
+constexpr int kHistStep = 16;                            // samples per load step
+constexpr int kHistBlock = kHistThreads * kHistSpan;     // samples per block
+
 template <int MODE>
-__global__ void __launch_bounds__(256, 3) mad_hist_kernel(const int32_t* D, int64_t pitch, int64_t n,
-                                                       BaselineCtx bc, int vec,
-                                                       uint32_t* __restrict__ hist, int32_t* Y,
-                                                       int64_t ypitch, int yvec) {
+__global__ void __launch_bounds__(kHistThreads, 4) mad_hist_kernel(const int32_t* D, int64_t pitch,
+                                                                int64_t n, BaselineCtx bc, int vec,
+                                                                uint32_t* __restrict__ hist,
+                                                                int32_t* Y, int64_t ypitch,
+                                                                int yvec) {
     __shared__ uint32_t h[kHistBins];
     const int trial = blockIdx.y;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const int32_t* row = D + (int64_t)trial * pitch;
     int32_t* yrow = Y + (int64_t)trial * ypitch;
-    const int64_t t_begin = (int64_t)blockIdx.x * kHistChunk + threadIdx.x * 32;
-    const int64_t t_end = min(n, t_begin + 32);
-    if (t_begin < t_end) {
-        int32_t v[32];
-        load_chunk32(row, t_begin, t_end, vec != 0, v);
+    const int64_t blk0 = (int64_t)blockIdx.x * kHistBlock;
+    // first sample of step 0 and the distance between steps
+    const int64_t s_first = blk0 + (int64_t)threadIdx.x * kHistSpan;
+    constexpr int64_t stride = kHistStep;
+    if (s_first < n) {
         Walker<MODE> w;
         w.setup(bc, row, n, trial);
-        w.init(t_begin);
+        w.init(s_first);
+        for (int j = 0; j < kHistSpan / kHistStep; ++j) {
+            const int64_t s = s_first + j * stride;
+            if (s >= n) break;
+            const int64_t t_end = min(n, s + kHistStep);
+            int32_t v[kHistStep];
+            const bool whole = s + kHistStep <= n;
+            if (vec && whole) {
+                const int4* p = reinterpret_cast<const int4*>(row + s);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            if (t_begin + q < t_end) {
-                const int32_t y = (int32_t)((int64_t)v[q] - w.value());
-                v[q] = y;
-                atomicAdd(&h[hist_bin(y < 0 ? -(int64_t)y : (int64_t)y)], 1u);
-                w.step();
+                for (int q = 0; q < kHistStep / 4; ++q) {
+                    const int4 x = __ldg(p + q);
+                    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kHistStep; ++q) v[q] = s + q < t_end ? row[s + q] : 0;
             }
-        }
-        if (yvec && t_end - t_begin == 32) {
-            int4* p = reinterpret_cast<int4*>(yrow + t_begin);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                p[q] = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
+            for (int q = 0; q < kHistStep; ++q) {
+                if (whole || s + q < t_end) {
+                    const int32_t y = (int32_t)((int64_t)v[q] - w.value());
+                    v[q] = y;
+                    const uint32_t m = y < 0 ? 0u - (uint32_t)y : (uint32_t)y;
+                    atomicAdd(&h[m < (uint32_t)kHistFine ? (int)m
+                                                         : kHistFine + (int)min(m >> 12, (uint32_t)(kHistFine - 1))],
+                              1u);
+                    w.step();
+                }
+            }
+            if (yvec && whole) {
+                int4* p = reinterpret_cast<int4*>(yrow + s);
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (t_begin + q < t_end) yrow[t_begin + q] = v[q];
+                for (int q = 0; q < kHistStep / 4; ++q)
+                    p[q] = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kHistStep; ++q)
+                    if (s + q < t_end) yrow[s + q] = v[q];
+            }
         }
     }
     __syncthreads();
@@ -725,20 +757,24 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
 
 // ------------------------------------------------ detection, 32-bit prefix
 // For trials whose every boxcar sum fits int32 (ybound * widest boxcar <
-// 2^31 - 1): 512 threads, each testing 8 consecutive starts, a tile of 4096
-// starts per block.  The prefix of y over the tile, 8 samples before it and
-// the widest boxcar after it is kept as wrapping 32-bit sums in shared memory
-// (a difference of two is the exact boxcar sum), with the tile's first start
-// at an index that is a multiple of 8: for a width that is a multiple of 8 a
-// thread reads the 8 sums it needs with two 16-byte loads, widths below 8 come
-// from the thread's own registers, and each start costs one subtract and one
-// compare per width.  The hot loop only records which widths had a start above
-// threshold; the rare warps with one find the run starts and follow each run
-// (as detect_kernel), runs leaving the halo go to tail_kernel.
-constexpr int kD32Threads = 512;
-constexpr int kD32Per = 8;                          // consecutive starts per thread
-constexpr int kD32Tile = kD32Threads * kD32Per;     // starts per block
-constexpr int kD32Lead = 8;                         // prefix entries before the first start
+// 2^31 - 1).  A block walks one segment of a trial's starts in chunks of 2048
+// (128 threads, 16 consecutive starts each), keeping the prefix of y as
+// wrapping 32-bit sums (a difference of two is the exact boxcar sum) in a
+// shared-memory ring that holds the chunk, 16 samples before it and the
+// widest boxcar after it.  Each chunk adds 2048 prefix entries, from loads
+// issued while the previous chunk was tested, so every sample is loaded and
+// summed once per segment.  A thread's first prefix index is a multiple of 16:
+// for a width that is a multiple of 16 it reads the 16 sums it needs with four
+// 16-byte loads (the 16-byte quarters of each 64-byte ring row are swizzled so
+// that the 8 lanes of a quarter-warp hit distinct banks), widths of 1, 2, 4, 8
+// and 16 come from its own registers, and a start costs one three-input add
+// and half a three-input AND per width.  The hot loop only notes that some
+// start is above threshold; the rare warps with one find the run starts and
+// follow each run (as detect_kernel), runs leaving the ring go to tail_kernel.
+constexpr int kDWThreads = 128;
+constexpr int kDWPer = 16;                          // consecutive starts per thread
+constexpr int kDWChunk = kDWThreads * kDWPer;       // starts per chunk
+constexpr int kDWLead = 16;                         // prefix entries before a segment's first start
 
 __device__ __forceinline__ uint32_t block_exclusive_scan32(uint32_t v, uint32_t* warp_tot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -763,218 +799,297 @@ __device__ __forceinline__ uint32_t block_exclusive_scan32(uint32_t v, uint32_t*
     return x - v + (warp > 0 ? warp_tot[warp - 1] : 0u);
 }
 
-// q[i] = the prefix W entries after p[i] for a width W below 8: from this
-// thread's own 8 entries p and the next 8, nx
+// q[i] = the prefix entry W after p[i], for W up to 16: from this thread's own
+// 16 entries p and the next 16, nx
 template <int W>
-__device__ __forceinline__ void shifted8(const uint32_t (&p)[8], const uint32_t (&nx)[8],
-                                         uint32_t (&q)[8]) {
+__device__ __forceinline__ void shifted16(const uint32_t (&p)[16], const uint32_t (&nx)[16],
+                                          uint32_t (&q)[16]) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) q[i] = i + W < 8 ? p[i + W] : nx[i + W - 8];
+    for (int i = 0; i < 16; ++i) q[i] = i + W < 16 ? p[i + W] : nx[i + W - 16];
 }
 
-__global__ void __launch_bounds__(kD32Threads) detect32_kernel(const __grid_constant__ SearchArgs a) {
-    extern __shared__ __align__(16) uint32_t A[];   // A[i] = sum of y over [base, base + i)
+// The prefix ring: entry k at position k & mask; the 16-byte quarter of each
+// 64-byte row is XOR-ed with bits 1-2 of the row index.
+struct Ring {
+    uint32_t* A;
+    int mask;
+    __device__ __forceinline__ static int swz(int r) { return r ^ (((r >> 5) & 3) << 2); }
+    __device__ __forceinline__ uint32_t get(int64_t k) const { return A[swz((int)(k & mask))]; }
+    // the 16 entries of the row at position r (a multiple of 16)
+    __device__ __forceinline__ void get16(int r, uint32_t (&v)[16]) const {
+        const int x = ((r >> 5) & 3) << 2;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint4 u = *reinterpret_cast<const uint4*>(&A[r + ((4 * h) ^ x)]);
+            v[4 * h] = u.x; v[4 * h + 1] = u.y; v[4 * h + 2] = u.z; v[4 * h + 3] = u.w;
+        }
+    }
+    __device__ __forceinline__ void put16(int r, const uint32_t (&v)[16]) const {
+        const int x = ((r >> 5) & 3) << 2;
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            *reinterpret_cast<uint4*>(&A[r + ((4 * h) ^ x)]) =
+                make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    }
+};
+
+__global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_constant__ SearchArgs a,
+                                                              int64_t seg, int ring_words) {
+    extern __shared__ __align__(16) uint32_t ring_mem[];
     __shared__ uint32_t warp_tot[32];
     __shared__ int32_t thr_s[kMaxWidths];           // INT32_MAX: this width finds nothing
     __shared__ int32_t width_s[kMaxWidths];
+    __shared__ int2 wt_s[kMaxWidths];               // {W, threshold} of the widths that can fire
+    __shared__ int nlive;
     const int trial = blockIdx.y;
     if (!narrow_trial(a, trial)) return;             // detect_kernel takes the trial
     const int64_t n = a.nout;
-    const int64_t t0 = (int64_t)blockIdx.x * kD32Tile;
-    const int64_t base = t0 - kD32Lead;
-    const int len = (int)min((int64_t)kD32Lead + kD32Tile + a.wmax, n - base);
+    const int64_t S0 = (int64_t)blockIdx.x * seg;    // this block's starts [S0, S1)
+    if (S0 >= n) return;
+    const int64_t S1 = min(n, S0 + seg);
+    const int64_t base = S0 - kDWLead;                // prefix entry k sums y over [base, base + k)
     const int32_t* yrow = a.Y + (int64_t)trial * a.ypitch;
+    const bool vec = (a.ypitch & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Ring R{ring_mem, ring_words - 1};
     if (tid < a.nw) {
         const int64_t tk = a.tint[(int64_t)trial * a.nw + tid];
         thr_s[tid] = (int32_t)min(tk, (int64_t)INT32_MAX);
         width_s[tid] = a.widths[tid];
     }
-    // the prefix: 8 consecutive samples per thread per pass, coalesced 16-byte
-    // loads where the row allows them; A[i] for i = 8 tid .. 8 tid + 7 holds the
-    // sum before sample base + i (entries past len repeat the total)
-    const bool vec = (a.ypitch & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0;
-    uint32_t carry = 0;
-    for (int p0 = 0; p0 < len; p0 += kD32Tile) {
-        const int i0 = p0 + kD32Per * tid;
-        const int64_t s0 = base + i0;
-        uint32_t v[8];
-        if (vec && s0 >= 0 && i0 + 8 <= len) {
-            const int4* q = reinterpret_cast<const int4*>(yrow + s0);
-            const int4 x = __ldg(q), y = __ldg(q + 1);
-            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-                v[e] = (i0 + e < len && s0 + e >= 0) ? (uint32_t)__ldg(yrow + s0 + e) : 0u;
+    if (tid == 0) {
+        int m = 0;
+        for (int k = 0; k < a.nw; ++k) {
+            const int64_t tk = a.tint[(int64_t)trial * a.nw + k];
+            if (tk < (int64_t)INT32_MAX) wt_s[m++] = make_int2(a.widths[k], (int)tk);
         }
-        uint32_t ex[8];
-        uint32_t run = 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            ex[e] = run;
-            run += v[e];
-        }
-        const uint32_t off = carry + block_exclusive_scan32(run, warp_tot);   // (synchronises)
-        if (i0 <= len) {   // entries up to len + 7 (the allocation holds them)
-            *reinterpret_cast<uint4*>(&A[i0]) =
-                make_uint4(off + ex[0], off + ex[1], off + ex[2], off + ex[3]);
-            *reinterpret_cast<uint4*>(&A[i0 + 4]) =
-                make_uint4(off + ex[4], off + ex[5], off + ex[6], off + ex[7]);
-        }
-        carry += warp_tot[kD32Threads / 32 - 1];
-        __syncthreads();   // warp_tot is rewritten by the next pass
+        nlive = m;
     }
-    if (tid == 0) A[len] = carry;
-    __syncthreads();
 
-    const int kb = kD32Lead + kD32Per * tid;          // prefix index of start tb
-    const int64_t tb = t0 + kD32Per * tid;            // this thread's first start
-    uint32_t p[8], nx[8];
-    {
-        const uint4 a0 = *reinterpret_cast<const uint4*>(&A[kb]);
-        const uint4 a1 = *reinterpret_cast<const uint4*>(&A[kb + 4]);
-        const uint4 b0 = *reinterpret_cast<const uint4*>(&A[kb + 8]);
-        const uint4 b1 = *reinterpret_cast<const uint4*>(&A[kb + 12]);
-        p[0] = a0.x; p[1] = a0.y; p[2] = a0.z; p[3] = a0.w;
-        p[4] = a1.x; p[5] = a1.y; p[6] = a1.z; p[7] = a1.w;
-        nx[0] = b0.x; nx[1] = b0.y; nx[2] = b0.z; nx[3] = b0.w;
-        nx[4] = b1.x; nx[5] = b1.y; nx[6] = b1.z; nx[7] = b1.w;
-    }
-    // the prefix W entries after each of this thread's starts
-    auto ahead = [&](int W, uint32_t (&q)[8]) {
-        if ((W & 7) == 0) {
-            const uint4 c0 = *reinterpret_cast<const uint4*>(&A[kb + W]);
-            const uint4 c1 = *reinterpret_cast<const uint4*>(&A[kb + W + 4]);
-            q[0] = c0.x; q[1] = c0.y; q[2] = c0.z; q[3] = c0.w;
-            q[4] = c1.x; q[5] = c1.y; q[6] = c1.z; q[7] = c1.w;
-        } else if (W < 8) {
-            switch (W) {
-                case 1: shifted8<1>(p, nx, q); break;
-                case 2: shifted8<2>(p, nx, q); break;
-                case 3: shifted8<3>(p, nx, q); break;
-                case 4: shifted8<4>(p, nx, q); break;
-                case 5: shifted8<5>(p, nx, q); break;
-                case 6: shifted8<6>(p, nx, q); break;
-                default: shifted8<7>(p, nx, q); break;
+    // y of the 16 samples before prefix entries f + 16 tid .. (0 outside the series)
+    uint32_t v[16];
+    auto load = [&](int64_t f) {
+        const int64_t s0 = base + f + kDWPer * tid;
+        if (vec && s0 >= 0 && s0 + 16 <= n) {
+            const int4* q = reinterpret_cast<const int4*>(yrow + s0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int4 x = __ldg(q + h);
+                v[4 * h] = x.x; v[4 * h + 1] = x.y; v[4 * h + 2] = x.z; v[4 * h + 3] = x.w;
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = A[kb + W + i];
+            for (int e = 0; e < 16; ++e)
+                v[e] = (s0 + e >= 0 && s0 + e < n) ? (uint32_t)__ldg(yrow + s0 + e) : 0u;
         }
     };
-    // hot loop: which widths have an above-threshold start among this thread's 8
-    uint32_t hit = 0;
-    for (int k = 0; k < a.nw; ++k) {
-        const int32_t thr = thr_s[k];
-        if (thr == INT32_MAX) continue;
-        const int W = width_s[k];
-        const int64_t lim = n - W - tb;               // starts tb + i, i <= lim, exist
-        uint32_t q[8];
-        ahead(W, q);
-        bool any = false;
-        if (lim >= 7) {
+    // prefix entries f .. f + kDWChunk - 1 from the loaded v (synchronises)
+    uint32_t carry = 0;
+    auto put = [&](int64_t f) {
+        uint32_t ex[16];
+        uint32_t run = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) any |= (int32_t)(q[i] - p[i]) >= thr;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) any |= i <= lim && (int32_t)(q[i] - p[i]) >= thr;
+        for (int e = 0; e < 16; ++e) {
+            ex[e] = run;
+            run += v[e];
         }
-        if (any) hit |= 1u << k;
+        const uint32_t off = carry + block_exclusive_scan32(run, warp_tot);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) ex[e] += off;
+        R.put16((int)((f + kDWPer * tid) & R.mask), ex);
+        carry += warp_tot[kDWThreads / 32 - 1];
+        __syncthreads();   // ring entries visible; warp_tot free for the next scan
+    };
+    // entries [0, f0) before the first chunk: the chunk, the lead and the widest boxcar
+    const int64_t f0 = (kDWLead + kDWChunk + (int64_t)a.wmax + 1 + kDWChunk - 1) / kDWChunk * kDWChunk;
+    int64_t f = 0;
+    for (; f < f0; f += kDWChunk) {
+        load(f);
+        put(f);
     }
+    const int64_t nchunks = (S1 - S0 + kDWChunk - 1) / kDWChunk;
+    if (nchunks > 1) load(f);                         // the next chunk's new samples, in flight
+    const bool cin_any = a.carry_in && S0 == 0;
 
-    // the block that holds start nwin - 1 reports the carry flags
-    if (a.carry_out && tid == 0 && a.nwin - 1 >= t0 && a.nwin - 1 < t0 + kD32Tile) {
-        const int i = (int)(a.nwin - 1 - base);
-        for (int k = 0; k < a.nw; ++k) {
-            const int W = width_s[k];
-            const bool above = thr_s[k] != INT32_MAX && a.nwin - 1 <= n - W &&
-                               (int32_t)(A[i + W] - A[i]) >= thr_s[k];
-            a.carry_out[(int64_t)trial * a.nw + k] = above ? 1 : 0;
-        }
-    }
-
-    if (!__any_sync(0xffffffffu, hit != 0)) return;
-    // rare: run starts and runs of the widths some lane flagged
-    unsigned todo = __reduce_or_sync(0xffffffffu, hit);
-    const bool cin_any = a.carry_in && t0 == 0;
-    while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int32_t thr = thr_s[k];
-        const int W = width_s[k];
-        const int64_t last = n - W;
-        const int64_t lim = last - tb;
-        uint32_t q[8];
-        ahead(W, q);
-        unsigned above = 0;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int64_t t0 = S0 + c * kDWChunk;
+        const int64_t kb = c * kDWChunk + kDWLead + kDWPer * tid;   // prefix index of start tb
+        const int64_t tb = t0 + kDWPer * tid;                        // this thread's first start
+        const int64_t tmax = S1 - 1;                                 // last start of the segment
+        const int64_t len = min(f - 1, n - base);                    // highest prefix entry held
+        const int pos0 = (int)(kb & R.mask);
+        uint32_t p[16], nx[16];
+        R.get16(pos0, p);
+        R.get16((pos0 + 16) & R.mask, nx);
+        // the prefix entry W after each of this thread's starts
+        auto ahead = [&](int W, uint32_t (&q)[16]) {
+            if ((W & 15) == 0) {
+                R.get16((pos0 + W) & R.mask, q);
+            } else if (W == 1) {
+                shifted16<1>(p, nx, q);
+            } else if (W == 2) {
+                shifted16<2>(p, nx, q);
+            } else if (W == 4) {
+                shifted16<4>(p, nx, q);
+            } else if (W == 8) {
+                shifted16<8>(p, nx, q);
+            } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (i <= lim && (int32_t)(q[i] - p[i]) >= thr) above |= 1u << i;
-        // a start opens a run when the start before it is below threshold; for
-        // this thread's first start that is the previous thread's last, or for
-        // the block's first start the start before the tile
-        const unsigned prev = __shfl_up_sync(0xffffffffu, above, 1);
-        bool left;
-        if (lane > 0) {
-            left = (prev >> 7) & 1u;
-        } else {
-            const int64_t tl = tb - 1;                // kb - 1 >= kD32Lead - 1 >= 0
-            left = tl >= 0 && tl <= last && (int32_t)(A[kb - 1 + W] - A[kb - 1]) >= thr;
-        }
-        unsigned starts = above & ~((above << 1) | (left ? 1u : 0u)) & 0xffu;
-        // streamed search: runs begin inside the window, and a run at start 0
-        // that the previous gulp left open is not reported again
-        if (a.nwin < tb + 8) starts &= a.nwin <= tb ? 0u : (1u << (int)(a.nwin - tb)) - 1u;
-        if (cin_any && tb == 0 && a.carry_in[(int64_t)trial * a.nw + k]) starts &= ~1u;
-        unsigned lanes = __ballot_sync(0xffffffffu, starts != 0);
-        auto box32 = [&](int64_t u) {
-            const int i = (int)(u - base);
-            return (int64_t)(int32_t)(A[i + W] - A[i]);
+                for (int i = 0; i < 16; ++i) q[i] = R.get(kb + W + i);
+            }
         };
-        while (lanes) {
-            const int L = __ffs(lanes) - 1;
-            lanes &= lanes - 1;
-            unsigned sL = __shfl_sync(0xffffffffu, starts, L);
-            const int64_t tL = t0 + (int64_t)kD32Per * (warp * 32 + L);
-            while (sL) {
-                const int e = __ffs(sL) - 1;
-                sL &= sL - 1;
-                int64_t bS, bt, tu = 0;
-                const bool tail = follow_run(tL + e, last, base, len, (int64_t)W, (int64_t)thr,
-                                             box32, lane, &bS, &bt, &tu);
-                if (lane == 0) {
-                    if (!tail) {
-                        emit(a, trial, k, bt, bS);
-                    } else {
-                        const unsigned long long qi = atomicAdd(
-                            reinterpret_cast<unsigned long long*>(a.tail_count), 1ull);
-                        if ((int64_t)qi < a.tail_cap) {
-                            TailRec r;
-                            r.trial = trial;
-                            r.k = k;
-                            r.u = tu;
-                            r.S_prev = box32(tu - 1);
-                            r.best_S = bS;
-                            r.best_t = bt;
-                            a.tails[qi] = r;
-                        } else {
-                            latch_status(a.status, HP_ERR_CAND_OVERFLOW);
+        // hot loop: does some width have an above-threshold start among this
+        // thread's 16?  When the whole chunk is valid for every width, the AND
+        // of S - thr over the starts has its sign bit clear iff some S >= thr (a
+        // wrapped difference can only add a false alarm, which the exact pass
+        // below clears); otherwise starts past the segment or the series are masked.
+        uint32_t hit = 0;
+        const bool full = t0 + kDWChunk - 1 <= tmax && t0 + kDWChunk - 1 <= n - a.wmax;
+        if (full) {
+            const int nl = nlive;
+            for (int k = 0; k < nl; ++k) {
+                const int2 wt = wt_s[k];
+                const uint32_t thr = (uint32_t)wt.y;
+                uint32_t q[16];
+                ahead(wt.x, q);
+                uint32_t acc = 0xffffffffu;
+#pragma unroll
+                for (int i = 0; i < 16; i += 2)
+                    acc &= (q[i] - p[i] - thr) & (q[i + 1] - p[i + 1] - thr);
+                if ((int32_t)acc >= 0) hit = 1u;
+            }
+            // the exact pass below wants the widths: find them on a hit (rare)
+            if (hit) {
+                hit = 0;
+                for (int k = 0; k < a.nw; ++k) {
+                    const int32_t thr = thr_s[k];
+                    if (thr == INT32_MAX) continue;
+                    uint32_t q[16];
+                    ahead(width_s[k], q);
+                    bool any = false;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) any |= (int32_t)(q[i] - p[i]) >= thr;
+                    if (any) hit |= 1u << k;
+                }
+            }
+        } else {
+            for (int k = 0; k < a.nw; ++k) {
+                const int32_t thr = thr_s[k];
+                if (thr == INT32_MAX) continue;
+                const int W = width_s[k];
+                const int64_t lim = min(tmax, n - W) - tb;   // starts tb + i, i <= lim, are tested
+                uint32_t q[16];
+                ahead(W, q);
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) any |= i <= lim && (int32_t)(q[i] - p[i]) >= thr;
+                if (any) hit |= 1u << k;
+            }
+        }
+
+        // the block that holds start nwin - 1 reports the carry flags
+        if (a.carry_out && tid == 0 && a.nwin - 1 >= t0 && a.nwin - 1 < t0 + kDWChunk &&
+            a.nwin - 1 < S1) {
+            const int64_t i = a.nwin - 1 - base;
+            for (int k = 0; k < a.nw; ++k) {
+                const int W = width_s[k];
+                const bool above = thr_s[k] != INT32_MAX && a.nwin - 1 <= n - W &&
+                                   (int32_t)(R.get(i + W) - R.get(i)) >= thr_s[k];
+                a.carry_out[(int64_t)trial * a.nw + k] = above ? 1 : 0;
+            }
+        }
+
+        if (__any_sync(0xffffffffu, hit != 0)) {
+            // rare: run starts and runs of the widths some lane flagged
+            unsigned todo = __reduce_or_sync(0xffffffffu, hit);
+            while (todo) {
+                const int k = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int32_t thr = thr_s[k];
+                const int W = width_s[k];
+                const int64_t last = n - W;
+                const int64_t lim = min(tmax, last) - tb;
+                uint32_t q[16];
+                ahead(W, q);
+                unsigned above = 0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (i <= lim && (int32_t)(q[i] - p[i]) >= thr) above |= 1u << i;
+                // a start opens a run when the start before it is below threshold:
+                // the previous lane's last start, or for lane 0 start tb - 1
+                const unsigned prev = __shfl_up_sync(0xffffffffu, above, 1);
+                bool left;
+                if (lane > 0) {
+                    left = (prev >> 15) & 1u;
+                } else {
+                    const int64_t tl = tb - 1;            // its prefix entry kb - 1 is held
+                    left = tl >= 0 && tl <= last &&
+                           (int32_t)(R.get(kb - 1 + W) - R.get(kb - 1)) >= thr;
+                }
+                unsigned starts = above & ~((above << 1) | (left ? 1u : 0u)) & 0xffffu;
+                // streamed search: runs begin inside the window, and a run at start 0
+                // that the previous gulp left open is not reported again
+                if (a.nwin < tb + 16) starts &= a.nwin <= tb ? 0u : (1u << (int)(a.nwin - tb)) - 1u;
+                if (cin_any && tb == 0 && a.carry_in[(int64_t)trial * a.nw + k]) starts &= ~1u;
+                unsigned lanes = __ballot_sync(0xffffffffu, starts != 0);
+                auto box32 = [&](int64_t u) {
+                    const int64_t i = u - base;
+                    return (int64_t)(int32_t)(R.get(i + W) - R.get(i));
+                };
+                while (lanes) {
+                    const int L = __ffs(lanes) - 1;
+                    lanes &= lanes - 1;
+                    unsigned sL = __shfl_sync(0xffffffffu, starts, L);
+                    const int64_t tL = t0 + (int64_t)kDWPer * (warp * 32 + L);
+                    while (sL) {
+                        const int e = __ffs(sL) - 1;
+                        sL &= sL - 1;
+                        int64_t bS, bt, tu = 0;
+                        const bool tail = follow_run(tL + e, last, base, len, (int64_t)W,
+                                                     (int64_t)thr, box32, lane, &bS, &bt, &tu);
+                        if (lane == 0) {
+                            if (!tail) {
+                                emit(a, trial, k, bt, bS);
+                            } else {
+                                const unsigned long long qi = atomicAdd(
+                                    reinterpret_cast<unsigned long long*>(a.tail_count), 1ull);
+                                if ((int64_t)qi < a.tail_cap) {
+                                    TailRec r;
+                                    r.trial = trial;
+                                    r.k = k;
+                                    r.u = tu;
+                                    r.S_prev = box32(tu - 1);
+                                    r.best_S = bS;
+                                    r.best_t = bt;
+                                    a.tails[qi] = r;
+                                } else {
+                                    latch_status(a.status, HP_ERR_CAND_OVERFLOW);
+                                }
+                            }
                         }
                     }
                 }
             }
+        }
+        __syncthreads();                              // chunk c tested everywhere
+        if (c + 1 < nchunks) {
+            put(f);                                   // the samples loaded during chunk c
+            f += kDWChunk;
+            if (c + 2 < nchunks) load(f);             // in flight while chunk c + 1 is tested
         }
     }
 }
 
 // Runs that leave the detect tile's halo: continue each one sample at a time
 // from the dedispersed row with exact baseline walkers, then emit it.
+// A warp per run, 32 starts per step: S(v) = S(v - 1) - y(v - 1) + y(v - 1 + W),
+// so the step's sums are S(u - 1) plus a warp prefix sum of those differences;
+// the run ends at the first start below threshold (or past the last start).
 __global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
     const int64_t cnt = min(*a.tail_count, a.tail_cap);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt;
-         q += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < cnt; q += warps) {
         const TailRec r = a.tails[q];
         const int64_t n = a.nout;
         const int32_t* yrow = a.Y + (int64_t)r.trial * a.ypitch;
@@ -982,14 +1097,32 @@ __global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
         const int64_t last = n - W;
         const int64_t thr = a.tint[(int64_t)r.trial * a.nw + r.k];
         int64_t best_S = r.best_S, best_t = r.best_t, Sp = r.S_prev;
-        for (int64_t v = r.u; v <= last; ++v) {
-            // y(v-1) leaves the window, y(v+W-1) enters it
-            const int64_t Sv = Sp - (int64_t)yrow[v - 1] + (int64_t)yrow[v - 1 + W];
-            if (Sv < thr) break;
-            if (Sv > best_S) { best_S = Sv; best_t = v; }
-            Sp = Sv;
+        for (int64_t v0 = r.u; v0 <= last; v0 += 32) {
+            const int64_t v = v0 + lane;
+            const bool inr = v <= last;
+            int64_t d = inr ? (int64_t)__ldg(yrow + v - 1 + W) - (int64_t)__ldg(yrow + v - 1) : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, d, o);
+                if (lane >= o) d += u;
+            }
+            const int64_t Sv = Sp + d;
+            const unsigned stop = __ballot_sync(0xffffffffu, !(inr && Sv >= thr));
+            const int first = stop ? __ffs(stop) - 1 : 32;
+            int64_t cs = lane < first ? Sv : LLONG_MIN, ct = v;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int64_t os = __shfl_down_sync(0xffffffffu, cs, o);
+                const int64_t ot = __shfl_down_sync(0xffffffffu, ct, o);
+                if (os > cs || (os == cs && ot < ct)) { cs = os; ct = ot; }
+            }
+            cs = __shfl_sync(0xffffffffu, cs, 0);
+            ct = __shfl_sync(0xffffffffu, ct, 0);
+            if (cs > best_S) { best_S = cs; best_t = ct; }
+            if (stop) break;
+            Sp = __shfl_sync(0xffffffffu, Sv, 31);
         }
-        emit(a, r.trial, r.k, best_t, best_S);
+        if (lane == 0) emit(a, r.trial, r.k, best_t, best_S);
     }
 }
 
@@ -1294,17 +1427,24 @@ cudaError_t launch_detect(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
     ++*nlaunch;
     detect_kernel<<<dgrid, kDetectThreads, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the trials whose boxcar sums all fit int32 (nearly all)
-    const size_t smem32 = ((size_t)kD32Lead + kD32Tile + (size_t)a.wmax + 16) * sizeof(uint32_t);
+    // the trials whose boxcar sums all fit int32 (nearly all): a block per
+    // segment of a trial, about 10 000 blocks, at least 4 chunks per segment
+    const int64_t f0 = ceil_div(kDWLead + kDWChunk + (int64_t)a.wmax + 1, kDWChunk) * kDWChunk;
+    int ring = 64;
+    while (ring < f0) ring <<= 1;
+    const size_t smem32 = (size_t)ring * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(detect32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem32)) != cudaSuccess)
         return e;
-    const dim3 dgrid32((unsigned)ceil_div(a.nout, kD32Tile), a.ndm);
+    const int64_t chunks = ceil_div(a.nout, kDWChunk);
+    const int64_t nseg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(10000, a.ndm), chunks / 4));
+    const int64_t seg = ceil_div(chunks, nseg) * kDWChunk;
+    const dim3 dgrid32((unsigned)ceil_div(a.nout, seg), a.ndm);
     ++*nlaunch;
-    detect32_kernel<<<dgrid32, kD32Threads, smem32, s>>>(a);
+    detect32_kernel<<<dgrid32, kDWThreads, smem32, s>>>(a, seg, ring);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
-    tail_kernel<<<64, 128, 0, s>>>(a);
+    tail_kernel<<<256, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1318,8 +1458,8 @@ cudaError_t launch_walkers(const SearchArgs& a, const BaselineCtx& bc, cudaStrea
     const int vec = ((a.pitch & 3) == 0) && (((uintptr_t)a.D & 15u) == 0);
     const int yvec = ((a.ypitch & 3) == 0) && (((uintptr_t)a.Y & 15u) == 0);
     ++*nlaunch;
-    mad_hist_kernel<MODE><<<hgrid, 256, 0, s>>>(a.D, a.pitch, n, bc, vec, a.hist, a.Y, a.ypitch,
-                                                yvec);
+    mad_hist_kernel<MODE><<<dim3((unsigned)ceil_div(n, kHistBlock), ndm), kHistThreads, 0, s>>>(
+        a.D, a.pitch, n, bc, vec, a.hist, a.Y, a.ypitch, yvec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
     mad_select_kernel<<<ndm, 1024, 0, s>>>(a.hist, n, a.refine_bucket, a.refine_rank, a.mad,
