@@ -17,6 +17,7 @@ bounded sample of trials of the same workload.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -72,6 +73,8 @@ def parse():
                     help="skip the decimated-boxcar variant's line")
     ap.add_argument("--decimate", type=int, default=16,
                     help="R of the decimated-boxcar variant")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the tiny and stress recipes' lines")
     ap.add_argument("--serve-beams", type=int, default=19)
     ap.add_argument("--serve-seconds", type=float, default=40.0,
                     help="seconds of real-time stream per beam")
@@ -114,6 +117,10 @@ def recovery_rates(w, pulses, cands):
     workloads.recovered), for matched S/N >= 10 and for 6-10."""
     from paper_2512_00398_gb300.workloads import recovered
     out = {}
+    if all(p.snr != p.snr for p in pulses):
+        # amplitudes given per channel (the tiny recipe): no nominal S/N
+        found = sum(1 for p in pulses if recovered(p, cands, w, snr_min=w.threshold))
+        return {"all": f"{found}/{len(pulses)}"}
     for name, lo, hi in (("snr>=10", 10.0, float("inf")), ("snr 6-10", 6.0, 10.0)):
         sel = [p for p in pulses if lo <= p.snr < hi]
         found = sum(1 for p in sel if recovered(p, cands, w, snr_min=w.threshold))
@@ -484,6 +491,8 @@ def run_ours(args):
         plan.close()
         torch.cuda.empty_cache()
         line["batch"] = run_batch(args, hp, torch, stream)
+    if world == 1 and not args.no_configs:
+        line["configs"] = run_configs(args, hp, torch, stream, peaks, hbm_peak)
     if world == 1 and not args.no_serve:
         line["serve"] = run_serve(args, hp, torch)
     if dist is not None:
@@ -705,6 +714,128 @@ def run_decimate(args, hp, torch, stream, w, s, fb, direct_cands, direct_ms, dir
     }
 
 
+# ------------------------------------------- the tiny and stress recipes
+def time_plan(hp, torch, plan, fb, stream, steps, warmup, capacity=1 << 16):
+    """ms per hp_search step (events around `steps` steps after `warmup`), then
+    per-stage ms from `steps` more with stage timing; returns the candidates."""
+    out = hp.new_cand_buf(capacity)
+    for _ in range(warmup):
+        hp.hp_search(plan, fb, stream, out=out)
+    st = hp.hp_plan_sync_status(plan, stream)
+    if st != hp.HP_OK:
+        raise hp.HPError(st, "warm-up")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        hp.hp_search(plan, fb, stream, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    hp.hp_plan_stats(plan, reset=True)
+    plan.set_param("stage_timing", 1)
+    for _ in range(steps):
+        hp.hp_search(plan, fb, stream, out=out)
+    st = hp.hp_plan_sync_status(plan, stream)
+    if st != hp.HP_OK:
+        raise hp.HPError(st, "timed steps")
+    stats = hp.hp_plan_stats(plan, reset=True)
+    plan.set_param("stage_timing", 0)
+    stages = {k: v / max(1, stats["stage_calls"][k]) for k, v in stats["stage_ms"].items()}
+    return ms, stages, hp.cands_to_numpy(*out)
+
+
+def config_line(w, ms, stages, cands, s, peaks, hbm_peak, nout):
+    """Throughput, real-time factor, rooflines and recovery of one recipe."""
+    o = w.obs
+    adds = float(w.ndm) * o.nchans * nout
+    se_bytes = 4.0 * w.ndm * nout * 3
+    peak_adds = 2.0 * peaks["int_add_ops_per_s"]
+    return {
+        "value": w.ndm * nout / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms,
+        "rtf": o.duration / (ms * 1e-3), "stages_ms": stages,
+        "roofline": {"bound": "alu", "kernel": "dedisp_rows_kernel",
+                     "achieved": adds / (stages["dedisp"] * 1e-3) / 1e12,
+                     "peak": peak_adds / 1e12, "unit": "Tadd/s",
+                     "frac": adds / (stages["dedisp"] * 1e-3) / peak_adds},
+        "search_roofline": {"bound": "hbm",
+                            "achieved_gbs": se_bytes / (stages["search"] * 1e-3) / 1e9,
+                            "peak_gbs": hbm_peak,
+                            "frac": se_bytes / (stages["search"] * 1e-3) / 1e9 / hbm_peak},
+        "clusters": int(len(cands)),
+        "recovery": recovery_rates(w, s.pulses, cands),
+    }
+
+
+def run_configs(args, hp, torch, stream, peaks, hbm_peak):
+    """The tiny recipe (128 ch, 32 768 samples, 100 trials) with the oracle timed
+    on the whole file and its clusters compared, and the stress recipe (4096 ch,
+    2^21 samples, ~4000 trials on DM 0-5000, boxcars to 8192, broadband spikes,
+    narrowband tones and drift), searched plain and with RFI mitigation, the
+    oracle timed on a sample of its trials."""
+    import oracle
+    from paper_2512_00398_gb300 import workloads
+    res = {}
+    # tiny: many steps (a search takes well under a millisecond)
+    w = workloads.tiny()
+    s = w.generate()
+    o = w.obs
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    nout = plan.nout(o.nsamps)
+    fb = torch.from_numpy(s.data).cuda()
+    ms, stages, cands = time_plan(hp, torch, plan, fb, stream, 200, 20)
+    line = config_line(w, ms, stages, cands, s, peaks, hbm_peak, nout)
+    t = time.perf_counter()
+    want = oracle.search(s.data, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
+    dt = time.perf_counter() - t
+    key = lambda c: (int(c["dm_idx"]), int(c["sample"]), int(c["width_idx"]))
+    line["oracle_equal"] = bool([key(c) for c in cands] == [key(c) for c in want.clusters] and
+                                np.abs(cands["snr"].astype(np.float64)
+                                       - want.clusters["snr"]).max() <= 1e-4)
+    line["cpu_baseline"] = {"value": w.ndm * nout / dt, "unit": METRIC,
+                            "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"the whole file (all {w.ndm} trials), {dt:.2f} s"}
+    line["workload"] = (f"tiny: {o.nchans} ch, {o.nsamps} samples at {o.tsamp * 1e6:.0f} us, "
+                        f"{w.ndm} trials on DM 0-400, boxcars 1..64, 3 pulses")
+    res["tiny"] = line
+    plan.close()
+    del fb
+    # stress: the raw list reaches ~6e7 (the drift's long-boxcar residuals)
+    w = workloads.stress()
+    s = w.generate(threads=min(16, os.cpu_count() or 8))
+    o = w.obs
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold,
+                   raw_capacity=1 << 26)
+    nout = plan.nout(o.nsamps)
+    plan.bind_workspace(o.nsamps)
+    fb = torch.from_numpy(s.data).cuda()
+    ms, stages, cands = time_plan(hp, torch, plan, fb, stream, 2, 1, capacity=1 << 24)
+    line = config_line(w, ms, stages, cands, s, peaks, hbm_peak, nout)
+    plan.set_param("rfi", 1)
+    ms_r, stages_r, cands_r = time_plan(hp, torch, plan, fb, stream, 2, 1, capacity=1 << 24)
+    line["with_rfi_mitigation"] = {"value": w.ndm * nout / (ms_r * 1e-3), "ms_per_step": ms_r,
+                                   "rfi_stage_ms": stages_r["rfi"], "clusters": int(len(cands_r)),
+                                   "recovery": recovery_rates(w, s.pulses, cands_r)}
+    plan.close()
+    del fb
+    torch.cuda.empty_cache()
+    dt1, units1, _ = oracle_sample(s, w, 1)
+    k = int(max(1, min(8, 12.0 / max(dt1, 1e-3))))
+    dtk, unitsk, _ = oracle_sample(s, w, k)
+    line["cpu_baseline"] = {"value": unitsk / dtk, "unit": METRIC, "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": f"{k} consecutive trials (of {w.ndm}) around the middle of "
+                                      f"the DM range, full {o.nsamps} samples, {dtk:.1f} s "
+                                      "(extrapolated to the whole file)"}
+    line["workload"] = (f"stress: {o.nchans} ch, {o.nsamps} samples ({o.duration:.1f} s), "
+                        f"{w.ndm} trials on DM 0-{float(w.dm_list[-1]):.0f}, boxcars 1..8192, "
+                        f"{len(s.pulses)} pulses, spikes, tones and drift")
+    res["stress"] = line
+    del s
+    return res
+
+
 # ------------------------------------------------------ batched vs plain
 def run_batch(args, hp, torch, stream):
     """The multi-file workload: 16 files of uneven length, channel count and
@@ -790,59 +921,138 @@ def run_batch(args, hp, torch, stream):
 
 
 # ------------------------------------------------------------- serving
+class GulpMaker:
+    """Every beam's gulps drawn on the device as they are needed: radiometer
+    noise from torch's generator seeded per (beam, gulp), the beam's dispersed
+    Gaussian pulses added (the signal model of synth: cold-plasma delays in
+    continuous time, signal added before quantisation), rounded and clipped
+    to uint8 and copied into a pinned host slot.  The serving measurement needs
+    19 independent beams at the real-time rate (1.6 GB/s of data), more than the
+    host generator makes; the device does it on a side stream in a few ms per
+    gulp."""
+
+    def __init__(self, torch, beams, G, slots_per_beam):
+        self.torch = torch
+        self.beams = beams
+        self.G = G
+        o = beams[0].obs
+        self.nch = o.nchans
+        self.stream = torch.cuda.Stream()
+        self.spb = slots_per_beam
+        self.slots = [[torch.empty((G, o.nchans), dtype=torch.uint8, pin_memory=True)
+                       for _ in range(slots_per_beam)] for _ in beams]
+        self.ready = [[None] * slots_per_beam for _ in beams]
+        self.freqs = o.freqs()
+
+    def make(self, b, g):
+        """Start gulp g of beam b; returns its slot index."""
+        torch = self.torch
+        w = self.beams[b]
+        o = w.obs
+        G = self.G
+        k = g % self.spb
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(1000003 * (b + 1) + g)
+        with torch.cuda.stream(self.stream):
+            x = torch.randn((G, self.nch), generator=gen, device="cuda", dtype=torch.float32)
+            x.mul_(o.sigma).add_(o.mean)
+            t0 = g * G * o.tsamp
+            t1 = (g + 1) * G * o.tsamp
+            for p in w.pulses:
+                tau = p.t0 + 4148.808 * p.dm * (self.freqs ** -2 - o.f_top ** -2)
+                half = 4.0 * p.fwhm
+                if tau.max() + half < t0 or tau.min() - half > t1:
+                    continue
+                rel = torch.from_numpy((tau - t0).astype(np.float32)).cuda()
+                tt = torch.arange(G, device="cuda", dtype=torch.float32) * o.tsamp
+                dt = (tt[:, None] - rel[None, :]) / p.fwhm
+                x.add_(torch.exp(dt.square_().mul_(-4.0 * math.log(2.0))).mul_(p.amp))
+            q = x.round_().clamp_(0, 255).to(torch.uint8)
+            self.slots[b][k].copy_(q, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        self.ready[b][k] = ev
+        return k
+
+    def get(self, b, g):
+        k = g % self.spb
+        self.ready[b][k].synchronize()
+        return self.slots[b][k]
+
+
 def run_serve(args, hp, torch):
     """The 19-beam stream: 4096 ch, 49.152 us, DM 0-2000, gulps of 65 536
-    samples (3.22 s).  Phase 1 pushes every beam's gulps at the real-time rate
-    (one gulp per beam every 3.22 s, each beam's arrival jittered by 0-20 ms)
-    and reports the gulp latency (push -> candidates in host memory).  Phase 2
-    pushes a backlog of gulps at once and reports the sustained throughput.
-    Gulp data cycle through a pool of 8 distinct synthetic gulps in pinned
-    host memory (generating 19 beams x minutes of data would take longer than
-    the measurement)."""
+    samples (3.22 s), every beam its own data (GulpMaker) with about one
+    injected pulse per beam-minute.  Phase 1 pushes every beam's gulps at the
+    real-time rate (one gulp per beam every 3.22 s, each beam's arrival jittered
+    by 0-20 ms) and reports the gulp latency (push -> candidates in host
+    memory) and the injection recovery; phase 2 pushes a backlog of gulps at
+    once and reports the sustained throughput."""
     import threading
     from paper_2512_00398_gb300 import workloads
+    from paper_2512_00398_gb300.workloads import recovered
     G = 65536
     nb = args.serve_beams
+    nb2 = 6                                           # backlog gulps per beam (phase 2)
     beams = workloads.serve(nbeams=nb, gulp=G, seconds=args.serve_seconds)
     w = beams[0]
     o = w.obs
-    pool_n = 8
-    poolw = workloads.serve(nbeams=1, gulp=G, seconds=pool_n * G * o.tsamp, seed0=900)[0]
-    pool_np = poolw.generate(threads=min(16, os.cpu_count() or 8)).data
-    pool = torch.from_numpy(pool_np).pin_memory()
-    del pool_np
-    gulps = [pool[i * G:(i + 1) * G] for i in range(pool_n)]
-    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
     tg = G * o.tsamp
+    ng = max(1, int(round(args.serve_seconds / tg)))
+    maker = GulpMaker(torch, beams, G, slots_per_beam=nb2 + 2)
+    plan = hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, w.threshold)
     budget = 120 * (1 << 30)
     st = hp.Stream(plan, nbeams=nb, gulp=G, hbm_budget=budget, cand_capacity=4096)
     info0 = st.stats()
     H = info0["tail_samples"]
+    done = [set() for _ in range(nb)]                 # gulps whose result came back
+    lock = threading.Lock()
+    cands = [[] for _ in range(nb)]
 
     def collect(n, out):
         while len(out) < n:
             r = st.poll(timeout_ms=600000)
             if r is None:
                 raise RuntimeError("stream stalled")
-            if r[0]["status"] != hp.HP_OK:
-                raise hp.HPError(r[0]["status"], "stream gulp")
-            out.append(r[0])
+            info, c = r
+            if info["status"] != hp.HP_OK:
+                raise hp.HPError(info["status"], "stream gulp")
+            out.append(info)
+            with lock:
+                done[info["beam"]].add(info["gulp_index"])
+            if len(c):
+                cands[info["beam"]].append(c)
 
-    # phase 1: real time
-    ng = max(1, int(round(args.serve_seconds / tg)))
+    def wait_slot(b, g):
+        """Slot g % slots may be reused once gulp g - slots has come back."""
+        old = g - maker.spb
+        while old >= 0:
+            with lock:
+                if old in done[b]:
+                    return
+            time.sleep(0.001)
+
+    # phase 1: real time, data made one gulp ahead
     rng = np.random.default_rng(17)
     jit = rng.uniform(0.0, 0.020, size=(ng, nb))
+    for b in range(nb):
+        maker.make(b, 0)
     res1 = []
-    t0 = time.perf_counter() + 0.2
+    t0 = time.perf_counter() + 0.5
 
     def producer():
         for g in range(ng):
             for b in np.argsort(jit[g]):
+                b = int(b)
                 t = t0 + (g + 1) * tg + jit[g, b]
                 d = t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                st.push(int(b), gulps[(int(b) * 3 + g) % pool_n])
+                st.push(b, maker.get(b, g))
+            if g + 1 < ng:
+                for b in range(nb):
+                    wait_slot(b, g + 1)
+                    maker.make(b, g + 1)
 
     th = threading.Thread(target=producer)
     th.start()
@@ -851,36 +1061,52 @@ def run_serve(args, hp, torch):
     searched = [r for r in res1 if r["window_len"] > 0]
     lat = np.array([r["latency_s"] for r in searched])
     units1 = sum(r["window_len"] for r in searched) * w.ndm
-    # phase 2: a backlog of 6 gulps per beam pushed at once
-    nb2 = 6
+    # injection recovery over the real-time phase (pulses fully inside it)
+    pulses, found = 0, 0
+    for b in range(nb):
+        cb = np.concatenate(cands[b]) if cands[b] else np.zeros(0, hp.CAND_DTYPE)
+        for p in beams[b].pulses:
+            if p.t0 + 5.0 > ng * tg or p.snr < 10.0:
+                continue
+            pulses += 1
+            found += recovered(p, cb, beams[b], snr_min=w.threshold)
+    # phase 2: a backlog of nb2 gulps per beam pushed at once
     res2 = []
+    for g in range(ng, ng + nb2):
+        for b in range(nb):
+            wait_slot(b, g)
+            maker.make(b, g)
+    torch.cuda.synchronize()
     t = time.perf_counter()
     for g in range(ng, ng + nb2):
         for b in range(nb):
-            st.push(b, gulps[(b * 3 + g) % pool_n])
+            st.push(b, maker.get(b, g))
     collect(nb2 * nb, res2)
     wall2 = time.perf_counter() - t
     units2 = sum(r["window_len"] for r in res2) * w.ndm
     stats = st.stats()
     st.close()
     plan.close()
-    del pool, gulps
+    del maker
     return {
         "workload": f"{nb} beams x {o.nchans} ch, {o.tsamp * 1e6:.3f} us, gulps of {G} samples "
                     f"({tg:.3f} s), {w.ndm} trials on DM 0-{float(w.dm_list[-1]):.0f}, boxcars "
                     f"1..{int(w.widths[-1])}, tail {H} samples, budget {budget >> 30} GiB; "
-                    f"data: {pool_n} distinct synthetic gulps in pinned host memory, cycled",
+                    f"data: every beam and gulp drawn separately on the device (seeded "
+                    f"noise + ~1 dispersed pulse per beam-minute), pinned host memory",
         "realtime": {"seconds": ng * tg, "gulps": len(res1), "searched": len(searched),
                      "latency_p50_s": float(np.percentile(lat, 50)) if lat.size else None,
                      "latency_p99_s": float(np.percentile(lat, 99)) if lat.size else None,
                      "latency_max_s": float(lat.max()) if lat.size else None,
                      "gulp_s": tg,
                      "rtf_p99": float(tg / np.percentile(lat, 99)) if lat.size else None,
-                     "value": units1 / (ng * tg), "unit": METRIC},
+                     "value": units1 / (ng * tg), "unit": METRIC,
+                     "recovery_snr_ge_10": f"{found}/{pulses}"},
         "saturated": {"gulps": len(res2), "wall_s": wall2, "value": units2 / wall2,
                       "unit": METRIC, "rtf": len(res2) * tg / wall2},
         "steps": stats["steps"], "max_batch_seen": stats["max_batch_seen"],
         "beam_slots": stats["beam_slots"], "device_gib": stats["device_bytes"] / (1 << 30),
+        "device_allocs_after_open": stats["device_allocs"] - info0["device_allocs"],
     }
 
 
