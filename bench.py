@@ -888,6 +888,8 @@ def run_batch(args, hp, torch, stream):
     t = time.perf_counter()
     cfg, tune_ms = b.autotune(fbs, stream)
     tune_s = time.perf_counter() - t
+    for p in plans:                                  # the plain path with the same tile shape
+        p.set_param("dedisp_config", cfg)
     bouts = [hp.new_cand_buf(1 << 16) for _ in files]
     batch_ms = timed(lambda: b.search_async(fbs, stream, outs=bouts))
     st = b.sync_status(stream)
@@ -895,6 +897,13 @@ def run_batch(args, hp, torch, stream):
         raise hp.HPError(st, "batched pass")
     got = [hp.cands_to_numpy(d, c) for d, c in bouts]
     identical = all(np.array_equal(g, w_) for g, w_ in zip(got, want))
+    # the spread: plain and batched passes alternated, each timed over `steps` passes
+    reps = []
+    for _ in range(5):
+        pm = timed(plain_pass)
+        bm = timed(lambda: b.search_async(fbs, stream, outs=bouts))
+        reps.append((pm, bm))
+    gains = sorted(pm / bm for pm, bm in reps)
     kernels = b.kernels_per_call()
     b.close()
     res = {
@@ -909,6 +918,10 @@ def run_batch(args, hp, torch, stream):
                     "rtf": dur / (batch_ms * 1e-3), "dedisp_config": cfg,
                     "autotune_s": tune_s, "kernels_per_call": kernels, "cuda_graph": True},
         "gain": plain_ms / batch_ms,
+        "gain_repeats": {"n": len(gains), "median": gains[len(gains) // 2], "min": gains[0],
+                         "max": gains[-1],
+                         "plain_ms": [pm for pm, _ in reps], "batched_ms": [bm for _, bm in reps],
+                         "basis": "plain and batched passes alternated, same tile shape"},
         "identical_candidates": bool(identical),
         "clusters": int(sum(len(x) for x in want)),
         "steps": steps,

@@ -168,7 +168,7 @@ int hp_plan_destroy(hp_plan* plan);
  * streams refuse it. */
 #define HP_PARAM_DECIMATE 15      /* R: 0 = every start (default) */
 
-#define HP_NUM_DEDISP_CONFIGS 17
+#define HP_NUM_DEDISP_CONFIGS 19
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);

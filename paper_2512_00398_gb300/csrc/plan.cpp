@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "plan_internal.h"
+#include "quad_tiling.h"
 
 using namespace hp;
 
@@ -290,6 +291,25 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
         T->cfg = cfg;
         return HP_OK;
     }
+    if (C.builders > 0) {
+        // quad patterns: the largest tile (up to BD trials) whose every quad fits a slot
+        int d0 = 0;
+        while (d0 < ndm) {
+            int nd = std::min(BD, ndm - d0);
+            const int32_t* base = &p->delays[(size_t)d0 * nch];
+            auto delay = [&](int j, int c) { return base[(size_t)j * nch + c]; };
+            for (;;) {
+                DedispTiling probe;
+                if (append_tile_quad(delay, nd, nch, d0, C, &probe) == HP_OK) break;
+                if (--nd == 0) return HP_ERR_INVALID_ARG;
+            }
+            const int rc = append_tile_quad(delay, nd, nch, d0, C, T);
+            if (rc) return rc;
+            d0 += nd;
+        }
+        T->cfg = cfg;
+        return HP_OK;
+    }
     int d0 = 0;
     while (d0 < ndm) {
         // grow the tile while every channel row alone still fits a stage
@@ -364,7 +384,8 @@ void apply_subband(hp_plan* p) {
 int64_t xt_pitch_for(int64_t nsamps) {
     int bt_max = 0;
     for (int i = 0; i < kNumDedispConfigs; ++i) bt_max = std::max(bt_max, kDedispConfigs[i].BT());
-    return round_up64(nsamps + bt_max + 32, 16);
+    // staged rows reach up to a tile plus a few words past the last delay
+    return round_up64(nsamps + bt_max + 128, 16);
 }
 
 
@@ -947,6 +968,7 @@ struct hp_batch {
     int cfg = hp::kDefaultDedispConfig;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> done;
+    std::vector<cudaEvent_t> dd_done;  // file i dedispersed (its search may start)
     cudaEvent_t fork = nullptr;
     // graph of the last argument set
     cudaGraphExec_t exec = nullptr;
@@ -985,29 +1007,31 @@ int batch_prepare(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
 
 // Enqueue the whole batch on s: one transpose launch, one dedispersion launch
 // over every file's tiles, then per file search + merge on a side stream.
+// One call of a batch: one transpose launch over every file; then the files'
+// dedispersion launches one after another on the caller's stream, largest
+// first, and each file's search and merge on its own side stream as soon as
+// its dedispersion is done -- so every search runs beside the dedispersion of
+// the files after it (the search stage is bound by HBM bandwidth, the
+// dedispersion by the integer and shared-memory pipes) -- joined back at the end.
 int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps, cudaStream_t s,
                   hp_cand_buf* outs, const std::vector<Layout>& Ls,
                   const std::vector<uint8_t*>& wss, int64_t* kernels) {
     const int n = (int)b->plans.size();
     TransposeBatch tb;
     std::memset(&tb, 0, sizeof(tb));
-    DedispBatch db;
-    std::memset(&db, 0, sizeof(db));
     tb.njobs = n;
-    int nd = 0;   // files dedispersed directly, in the one batched launch
+    std::vector<int> order;
+    std::vector<int64_t> work(n, 0);
     for (int i = 0; i < n; ++i) {
         hp_plan* p = b->plans[i];
         const Layout& L = Ls[i];
         tb.jobs[i] = make_transpose_job(fbs[i], nsamps[i], p->nchans, wss[i] + L.xt, L.xt_pitch);
         tb.prefix[i + 1] = tb.prefix[i] + tb.jobs[i].ttiles * tb.jobs[i].ctiles;
-        if (p->sb_chans > 0) continue;      // the sub-band variant runs its own two stages
-        if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
-        db.jobs[nd] = make_job(p, wss[i] + L.xt, L.xt_pitch, (int32_t*)(wss[i] + L.D), L.dpitch,
-                               L.nout);
-        db.prefix[nd + 1] = db.prefix[nd] + (int64_t)db.jobs[nd].ntt * db.jobs[nd].ndt;
-        ++nd;
+        if (p->sb_chans <= 0 && !reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
+        work[i] = (int64_t)p->ndm() * p->nchans * std::max<int64_t>(L.nout, 0);
+        order.push_back(i);
     }
-    db.njobs = nd;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
     int64_t k = 0;
     int rc = check_cuda(launch_transpose_batch(tb, s));
     if (rc) return rc;
@@ -1021,29 +1045,29 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         rc = check_cuda(launch_rfi(r, s, &k));
         if (rc) return rc;
     }
-    hp_plan* p0 = b->plans[0];
-    if (nd > 0) {
-        rc = check_cuda(launch_dedisp(b->cfg, db, p0->status, p0->timeout_ns, s));
-        if (rc) return rc;
-        ++k;
-    }
-    for (int i = 0; i < n; ++i) {
-        hp_plan* p = b->plans[i];
-        if (p->sb_chans <= 0) continue;
-        const Layout& L = Ls[i];
-        const int64_t before = p->launches;
-        rc = run_subband(p, L, wss[i], (int32_t*)(wss[i] + L.D), L.dpitch, s);
-        if (rc) return rc;
-        k += p->launches - before;
-    }
-    rc = check_cuda(cudaEventRecord(b->fork, s));
-    if (rc) return rc;
-    for (int i = 0; i < n; ++i) {
+    for (int i : order) {
         hp_plan* p = b->plans[i];
         const Layout& L = Ls[i];
         uint8_t* ws = wss[i];
+        if (p->sb_chans > 0) {             // the sub-band variant runs its own two stages
+            const int64_t before = p->launches;
+            rc = run_subband(p, L, ws, (int32_t*)(ws + L.D), L.dpitch, s);
+            if (rc) return rc;
+            k += p->launches - before;
+        } else {
+            DedispBatch db;
+            std::memset(&db, 0, sizeof(db));
+            db.njobs = 1;
+            db.jobs[0] = make_job(p, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, L.nout);
+            db.prefix[1] = (int64_t)db.jobs[0].ntt * db.jobs[0].ndt;
+            rc = check_cuda(launch_dedisp(b->cfg, db, p->status, p->timeout_ns, s));
+            if (rc) return rc;
+            ++k;
+        }
+        rc = check_cuda(cudaEventRecord(b->dd_done[i], s));
+        if (rc) return rc;
         cudaStream_t si = b->side[i];
-        rc = check_cuda(cudaStreamWaitEvent(si, b->fork, 0));
+        rc = check_cuda(cudaStreamWaitEvent(si, b->dd_done[i], 0));
         if (rc) return rc;
         hp_raw_cand* raw = (hp_raw_cand*)(ws + L.raw);
         int64_t* raw_count = (int64_t*)(ws + L.raw_count);
@@ -1057,6 +1081,8 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         if (rc) return rc;
         rc = check_cuda(cudaEventRecord(b->done[i], si));
         if (rc) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
         rc = check_cuda(cudaStreamWaitEvent(s, b->done[i], 0));
         if (rc) return rc;
     }
@@ -1524,6 +1550,8 @@ int hp_batch_create(hp_batch** out, hp_plan* const* plans, int nfiles) {
         b->side.push_back(st);
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { rc = HP_ERR_CUDA; break; }
         b->done.push_back(ev);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { rc = HP_ERR_CUDA; break; }
+        b->dd_done.push_back(ev);
     }
     if (rc) {
         hp_batch_destroy(b);
@@ -1539,6 +1567,7 @@ int hp_batch_destroy(hp_batch* b) {
     batch_drop_graph(b);
     for (cudaStream_t st : b->side) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : b->dd_done) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return HP_OK;
