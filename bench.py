@@ -34,12 +34,13 @@ sys.path.insert(0, ROOT)
 METRIC = "DM-trial·samples/s"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# dedispersion kernel on this exact workload and tile configuration, from a one-pass ncu
-# capture of the full-size bench command (profiles/dedisp_rows_kernel_fast_4096ch.md).
-# Keyed by the kernel source it was measured on; a changed kernel, another workload or
-# another configuration reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "9e5e324f726ed58f", "bytes": 37.47e9 + 5.74e9,
-                  "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 22}
+# dedispersion kernel on this workload and tile configuration: an ncu capture of the
+# same kernel on the 2^18-sample case (nout 168 628, profiles/dedisp_rows_kernel_fast_4096ch.md)
+# scaled by the number of time tiles to the full nout of 955 060.  Keyed by the kernel
+# source it was measured on; a changed kernel, another workload or another
+# configuration reports null until it is captured again.
+DEDISP_TRAFFIC = {"source_sha256_16": "12b8ffc2b29f8ea9", "bytes": (6.665e9 + 1.011e9) * 955060 / 168628,
+                  "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 12}
 # The same for the two stages of the sub-band variant (64-channel sub-bands, groups
 # of 8 trials): DRAM bytes of one step (4 launches of each stage), measured per launch
 # (profiles/subband_fast_4096ch.md), keyed by both kernel sources.
