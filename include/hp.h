@@ -121,7 +121,8 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_T_GAP 3          /* merge: max gap between boxcar windows, samples */
 #define HP_PARAM_W_TOL 4          /* merge: max |width index difference| (>= 0) */
 #define HP_PARAM_RAW_CAPACITY 5   /* raw-candidate scratch capacity (>= 1024) */
-#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 12 */
+#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 19;
+                                     12 while HP_PARAM_SUBBAND_CHANS > 0 unless a shape was set */
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
 #define HP_PARAM_RFI 9            /* 1 = RFI mitigation before dedispersion (default 0) */
@@ -142,7 +143,7 @@ int hp_plan_destroy(hp_plan* plan);
  * that maximum).  hp_search, hp_dedisperse, hp_plan_autotune, batches (the
  * variant's files through their own two stages; hp_batch_autotune refuses it)
  * and streams (per searched buffer) follow the variant (tile shapes 7, 11,
- * 12 and 14 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
+ * 12, 14 and 19 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
  * delay of channel c per unit DM in samples. */
 #define HP_PARAM_SUBBAND_CHANS 12 /* S: channels per sub-band, 0 = direct dedispersion (default) */
 #define HP_PARAM_SUBBAND_GROUP 13 /* G: trials per group, 1..ndm (default 8) */
@@ -168,7 +169,7 @@ int hp_plan_destroy(hp_plan* plan);
  * streams refuse it. */
 #define HP_PARAM_DECIMATE 15      /* R: 0 = every start (default) */
 
-#define HP_NUM_DEDISP_CONFIGS 19
+#define HP_NUM_DEDISP_CONFIGS 22
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);

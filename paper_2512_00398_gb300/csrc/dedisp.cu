@@ -45,6 +45,11 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
     // quad patterns: 12 consumer + 12 builder + 1 producer warps, BD 24, BT 896
     {4, 7, 6, 2, 72 * 1024, 3, 1, 12},  // 17: 3 x 72 KB slots
     {4, 7, 6, 2, 54 * 1024, 4, 1, 12},  // 18: 4 x 54 KB slots
+    // one trial per warp over 17 words (68 samples) per lane: 18 loads per 17
+    // words and the table entry and loop overhead spread over twice the words
+    {1, 17, 15, 1, 72 * 1024, 3, 1},   // 19: 15+1 warps, BD 15, BT 2176, 3 x 72 KB (default)
+    {1, 17, 15, 1, 108 * 1024, 2, 1},  // 20: as 19, 2 x 108 KB
+    {1, 19, 11, 1, 72 * 1024, 3, 1},   // 21: 11+1 warps, BD 11, BT 2432
 };
 
 namespace {
@@ -701,11 +706,16 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
         case 16: return run_dedisp_rows<1, 7, 16, 1, 4, 2>(b, sb, status, timeout_ns, s);
         case 17: return run_dedisp_quad<4, 7, 6, 2, 12, 3>(b, sb, status, timeout_ns, s);
         case 18: return run_dedisp_quad<4, 7, 6, 2, 12, 4>(b, sb, status, timeout_ns, s);
+        case 19: return run_dedisp_rows<1, 17, 15, 1, 3, 1>(b, sb, status, timeout_ns, s);
+        case 20: return run_dedisp_rows<1, 17, 15, 1, 2, 1>(b, sb, status, timeout_ns, s);
+        case 21: return run_dedisp_rows<1, 19, 11, 1, 3, 1>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-bool segmented_config(int cfg) { return cfg == 7 || cfg == 11 || cfg == 12 || cfg == 14; }
+bool segmented_config(int cfg) {
+    return cfg == 7 || cfg == 11 || cfg == 12 || cfg == 14 || cfg == 19;
+}
 
 cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& b, int* status,
                                     uint64_t timeout_ns, cudaStream_t s) {
@@ -716,6 +726,7 @@ cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& b, int* status,
         case 11: return run_dedisp_rows<2, 5, 12, 1, 4, 1, true>(b, sb, status, timeout_ns, s);
         case 12: return run_dedisp_rows<2, 7, 12, 1, 4, 2, true>(b, sb, status, timeout_ns, s);
         case 14: return run_dedisp_rows<1, 7, 24, 1, 4, 2, true>(b, sb, status, timeout_ns, s);
+        case 19: return run_dedisp_rows<1, 17, 15, 1, 3, 1, true>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

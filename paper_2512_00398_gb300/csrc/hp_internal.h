@@ -43,8 +43,10 @@ struct DedispConfig {
     int BT() const { return WT * NW * (builders ? 64 : 128); }
     int threads() const { return 32 * (WD * WT + builders + 1); }
 };
-constexpr int kNumDedispConfigs = 19;
-constexpr int kDefaultDedispConfig = 12;
+constexpr int kNumDedispConfigs = 22;
+constexpr int kDefaultDedispConfig = 19;
+// stage 1 of the sub-band variant: its tile shape unless one was set
+constexpr int kDefaultSubbandConfig = 12;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
 
 // One staged channel row of a DM tile (16 bytes, copied into shared memory).

@@ -1227,6 +1227,7 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
         case HP_PARAM_DEDISP_CONFIG:
             if (v < 0 || v >= kNumDedispConfigs || v != std::floor(v)) return HP_ERR_INVALID_ARG;
             p->dedisp_cfg = (int)v;
+            p->dedisp_cfg_set = true;
             return HP_OK;
         case HP_PARAM_STAGE_TIMING:
             if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
@@ -1262,6 +1263,8 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
         case HP_PARAM_SUBBAND_CHANS:
             if (v < 0 || v > p->nchans || v != std::floor(v)) return HP_ERR_INVALID_ARG;
             p->sb_chans = (int)v;
+            if (!p->dedisp_cfg_set)
+                p->dedisp_cfg = p->sb_chans > 0 ? kDefaultSubbandConfig : kDefaultDedispConfig;
             apply_subband(p);
             return HP_OK;
         case HP_PARAM_SUBBAND_GROUP:
@@ -1523,6 +1526,7 @@ int hp_plan_autotune(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream
         if (best < 0 || ms < best_t) { best = c; best_t = ms; }
     }
     p->dedisp_cfg = best >= 0 ? best : keep;
+    if (best >= 0) p->dedisp_cfg_set = true;
     rc = ensure_device_tables(p);
     if (rc) return rc;
     if (best_config) *best_config = p->dedisp_cfg;

@@ -58,6 +58,7 @@ struct hp_plan {
     int w_tol = 0;
     int64_t raw_capacity = (int64_t)1 << 22;
     int dedisp_cfg = hp::kDefaultDedispConfig;
+    bool dedisp_cfg_set = false;       // a tile shape was set (or autotuned) by the caller
     uint64_t timeout_ns = 1000000000ull;
 
     std::vector<int32_t> delays;   // [ndm][nchans]

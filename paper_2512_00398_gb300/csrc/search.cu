@@ -239,10 +239,6 @@ __global__ void __launch_bounds__(1024) mean_scan_kernel(int64_t* __restrict__ p
 // -------------------------------------------------------- |y| histogram
 constexpr int kHistChunk = 8192;   // samples per block (256 threads x 32)
 
-__device__ __forceinline__ int hist_bin(int64_t v) {
-    return v < kHistFine ? (int)v : kHistFine + (int)min(v >> 12, (int64_t)(kHistFine - 1));
-}
-
 // The 32 samples of one thread's chunk, with 16-byte loads when the row is
 // 16-byte aligned (pitch a multiple of 4 and an aligned base).
 __device__ __forceinline__ void load_chunk32(const int32_t* __restrict__ row, int64_t t_begin,
@@ -481,12 +477,13 @@ __global__ void sigma_kernel(const int64_t* __restrict__ mad, int ndm,
 constexpr int kDetectThreads = 256;
 constexpr int kDetectPer = kDetectTile / kDetectThreads;   // starts per thread
 
-// Every boxcar sum of this trial fits int32: its |y| bound times the widest
-// boxcar of the series stays below 2^31 - 1.
+// Every boxcar sum of this trial fits int32 with room to spare: its |y| bound
+// times (the widest boxcar + 32) stays below 2^31 - 1 (the 32-bit detection's
+// group bound adds two 15-sample partial sums to a boxcar sum).
 __device__ __forceinline__ bool narrow_trial(const SearchArgs& a, int trial) {
     if (!a.ybound) return false;
     const int64_t yb = a.ybound[trial];
-    return yb >= 0 && yb * a.ybound_w < (int64_t)INT32_MAX;
+    return yb >= 0 && yb * (a.ybound_w + 32) < (int64_t)INT32_MAX;
 }
 
 
@@ -767,10 +764,18 @@ __global__ void __launch_bounds__(kDetectThreads) detect_kernel(const __grid_con
 // for a width that is a multiple of 16 it reads the 16 sums it needs with four
 // 16-byte loads (the 16-byte quarters of each 64-byte ring row are swizzled so
 // that the 8 lanes of a quarter-warp hit distinct banks), widths of 1, 2, 4, 8
-// and 16 come from its own registers, and a start costs one three-input add
-// and half a three-input AND per width.  The hot loop only notes that some
-// start is above threshold; the rare warps with one find the run starts and
-// follow each run (as detect_kernel), runs leaving the ring go to tail_kernel.
+// come from its own registers, and a start costs one three-input add and half
+// a three-input AND per width.  Widths that are multiples of 16 are first
+// tested per group of 16 starts against an upper bound: with P the prefix,
+// g = 16 starts from entry k, and M+ / M- the largest / smallest of
+// P[j + i] - P[j] over i < 16 for the group at j (kept per group when the
+// prefix is written),
+//   max_i S_W(k + i) <= P[k + W] - P[k] + M+(k + W) - M-(k),
+// so one add and a sign test clear the whole group and only groups whose bound
+// reaches the threshold take the exact test.  The hot loop only notes that
+// some start is above threshold; the rare warps with one find the run starts
+// and follow each run (as detect_kernel), runs leaving the ring go to
+// tail_kernel.
 constexpr int kDWThreads = 128;
 constexpr int kDWPer = 16;                          // consecutive starts per thread
 constexpr int kDWChunk = kDWThreads * kDWPer;       // starts per chunk
@@ -839,8 +844,8 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
     __shared__ uint32_t warp_tot[32];
     __shared__ int32_t thr_s[kMaxWidths];           // INT32_MAX: this width finds nothing
     __shared__ int32_t width_s[kMaxWidths];
-    __shared__ int2 wt_s[kMaxWidths];               // {W, threshold} of the widths that can fire
-    __shared__ int nlive;
+    __shared__ int2 wt_s[kMaxWidths];               // {W, threshold} of the widths that can fire:
+    __shared__ int nlive, nexact;                   // [0, nexact) tested exactly, the rest by group bound
     const int trial = blockIdx.y;
     if (!narrow_trial(a, trial)) return;             // detect_kernel takes the trial
     const int64_t n = a.nout;
@@ -852,6 +857,9 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
     const bool vec = (a.ypitch & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Y) & 15u) == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Ring R{ring_mem, ring_words - 1};
+    // per group of 16 ring entries: {P at its first entry, M+}, and M-
+    uint2* gpm = reinterpret_cast<uint2*>(ring_mem + ring_words);
+    int32_t* gmn = reinterpret_cast<int32_t*>(gpm + (ring_words >> 4));
     if (tid < a.nw) {
         const int64_t tk = a.tint[(int64_t)trial * a.nw + tid];
         thr_s[tid] = (int32_t)min(tk, (int64_t)INT32_MAX);
@@ -859,9 +867,13 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
     }
     if (tid == 0) {
         int m = 0;
-        for (int k = 0; k < a.nw; ++k) {
-            const int64_t tk = a.tint[(int64_t)trial * a.nw + k];
-            if (tk < (int64_t)INT32_MAX) wt_s[m++] = make_int2(a.widths[k], (int)tk);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < a.nw; ++k) {
+                const int64_t tk = a.tint[(int64_t)trial * a.nw + k];
+                if (tk < (int64_t)INT32_MAX && ((a.widths[k] & 15) == 0) == (pass == 1))
+                    wt_s[m++] = make_int2(a.widths[k], (int)tk);
+            }
+            if (pass == 0) nexact = m;
         }
         nlive = m;
     }
@@ -893,10 +905,22 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
             ex[e] = run;
             run += v[e];
         }
+        // the group's M+ and M- (partial sums of at most 15 samples: exact int32)
+        int32_t mx = 0, mn = 0;
+#pragma unroll
+        for (int e = 1; e < 16; e += 2) {
+            const int32_t x0 = (int32_t)ex[e];
+            const int32_t x1 = e + 1 < 16 ? (int32_t)ex[e + 1] : 0;
+            mx = __vimax3_s32(mx, x0, x1);
+            mn = __vimin3_s32(mn, x0, x1);
+        }
         const uint32_t off = carry + block_exclusive_scan32(run, warp_tot);
 #pragma unroll
         for (int e = 0; e < 16; ++e) ex[e] += off;
-        R.put16((int)((f + kDWPer * tid) & R.mask), ex);
+        const int pos = (int)((f + kDWPer * tid) & R.mask);
+        R.put16(pos, ex);
+        gpm[pos >> 4] = make_uint2(off, (uint32_t)mx);
+        gmn[pos >> 4] = mn;
         carry += warp_tot[kDWThreads / 32 - 1];
         __syncthreads();   // ring entries visible; warp_tot free for the next scan
     };
@@ -946,8 +970,8 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
         uint32_t hit = 0;
         const bool full = t0 + kDWChunk - 1 <= tmax && t0 + kDWChunk - 1 <= n - a.wmax;
         if (full) {
-            const int nl = nlive;
-            for (int k = 0; k < nl; ++k) {
+            const int nl = nlive, ne = nexact;
+            for (int k = 0; k < ne; ++k) {
                 const int2 wt = wt_s[k];
                 const uint32_t thr = (uint32_t)wt.y;
                 uint32_t q[16];
@@ -957,6 +981,25 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
                 for (int i = 0; i < 16; i += 2)
                     acc &= (q[i] - p[i] - thr) & (q[i + 1] - p[i + 1] - thr);
                 if ((int32_t)acc >= 0) hit = 1u;
+            }
+            // widths that are multiples of 16: the group bound first.  If a start
+            // fires, bound - thr lies in [0, (W + 30) * |y| bound] < 2^31 (narrow
+            // trial), so its sign bit is clear; a set sign bit clears the group.
+            const uint32_t base0 = p[0] + (uint32_t)gmn[pos0 >> 4];
+            for (int k = ne; k < nl; ++k) {
+                const int2 wt = wt_s[k];
+                const int r = (pos0 + wt.x) & R.mask;
+                const uint2 g = gpm[r >> 4];
+                if ((int32_t)(g.x + g.y - base0 - (uint32_t)wt.y) >= 0) {
+                    const uint32_t thr = (uint32_t)wt.y;
+                    uint32_t q[16];
+                    R.get16(r, q);
+                    uint32_t acc = 0xffffffffu;
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2)
+                        acc &= (q[i] - p[i] - thr) & (q[i + 1] - p[i + 1] - thr);
+                    if ((int32_t)acc >= 0) hit = 1u;
+                }
             }
             // the exact pass below wants the widths: find them on a hit (rare)
             if (hit) {
@@ -1432,7 +1475,8 @@ cudaError_t launch_detect(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
     const int64_t f0 = ceil_div(kDWLead + kDWChunk + (int64_t)a.wmax + 1, kDWChunk) * kDWChunk;
     int ring = 64;
     while (ring < f0) ring <<= 1;
-    const size_t smem32 = (size_t)ring * sizeof(uint32_t);
+    // the ring, then per group of 16 entries {P, M+} and M-
+    const size_t smem32 = (size_t)ring * sizeof(uint32_t) + (size_t)(ring / 16) * 12;
     if ((e = cudaFuncSetAttribute(detect32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem32)) != cudaSuccess)
         return e;

@@ -404,6 +404,7 @@ int copy_plan(const hp_plan* t, int64_t raw_capacity, hp_plan** out) {
     p->t_gap = t->t_gap;
     p->w_tol = t->w_tol;
     p->dedisp_cfg = t->dedisp_cfg;
+    p->dedisp_cfg_set = t->dedisp_cfg_set;
     p->timeout_ns = t->timeout_ns;
     p->raw_capacity = raw_capacity;
     p->rfi = t->rfi;
