@@ -202,12 +202,15 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
     // the next group: the blocks resident together read neighbouring windows of
     // the same channel rows, which L2 then serves (DM-tile-major order re-reads
     // the whole input from DRAM once per DM tile).
-    const int64_t per = (int64_t)kTimeGroup * J.ndt;
+    // (half as many of the long tiles of 2048 samples and more, so that a group's
+    // row windows still fit in L2)
+    constexpr int TG = BT >= 2048 ? kTimeGroup / 2 : kTimeGroup;
+    const int64_t per = (int64_t)TG * J.ndt;
     const int64_t grp = item / per;
     const int64_t rem = item - grp * per;
-    const int64_t gsz = min((int64_t)kTimeGroup, (int64_t)J.ntt - grp * kTimeGroup);
+    const int64_t gsz = min((int64_t)TG, (int64_t)J.ntt - grp * TG);
     const int dt = (int)(rem / gsz);
-    const int tt = (int)(grp * kTimeGroup + rem % gsz);
+    const int tt = (int)(grp * TG + rem % gsz);
     const TileDesc T = J.tiles[dt];
     const int64_t t0 = (int64_t)tt * BT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

@@ -49,84 +49,110 @@ __constant__ int64_t kPow5[14] = {1, 5, 25, 125, 625, 3125, 15625, 78125, 390625
                                   9765625, 48828125, 244140625, 1220703125};
 
 // q (<= 5) remedian levels over chunks of 5^q values; one value per chunk.
-__global__ void __launch_bounds__(256) remedian_pass_kernel(const int32_t* __restrict__ in,
-                                                            int64_t in_pitch, int64_t n_in, int q,
-                                                            int32_t* __restrict__ out,
-                                                            int64_t out_pitch) {
+// A block takes the chunks blockIdx.x, blockIdx.x + gridDim.x, ... of one
+// trial; the loads of its next chunk are in flight while the current chunk's
+// levels are formed in shared memory.
+constexpr int kRemThreads = 256;
+constexpr int kRemPer = (3125 + kRemThreads - 1) / kRemThreads;   // values per thread
+constexpr int kRemChunksPerBlock = 8;
+
+__global__ void __launch_bounds__(kRemThreads) remedian_pass_kernel(const int32_t* __restrict__ in,
+                                                                   int64_t in_pitch, int64_t n_in,
+                                                                   int q, int32_t* __restrict__ out,
+                                                                   int64_t out_pitch, int64_t n_out) {
     __shared__ int32_t buf[2][3125];
     const int trial = blockIdx.y;
     const int64_t chunk = kPow5[q];
-    const int64_t base = (int64_t)blockIdx.x * chunk;
-    int cnt = (int)min(chunk, n_in - base);
-    const int32_t* src = in + (int64_t)trial * in_pitch + base;
-    constexpr int kLoadBatch = 8;   // independent loads in flight per thread
-    for (int ib = threadIdx.x; ib < cnt; ib += kLoadBatch * blockDim.x) {
-        int32_t v[kLoadBatch];
+    const int32_t* row = in + (int64_t)trial * in_pitch;
+    int32_t v[kRemPer];
+    auto load = [&](int64_t c) {
+        const int64_t base = c * chunk;
+        const int cnt = (int)min(chunk, n_in - base);
 #pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-            const int i = ib + u * (int)blockDim.x;
-            v[u] = i < cnt ? __ldg(src + i) : 0;
+        for (int u = 0; u < kRemPer; ++u) {
+            const int i = (int)threadIdx.x + u * kRemThreads;
+            v[u] = i < cnt ? __ldg(row + base + i) : 0;
         }
+    };
+    int64_t c = blockIdx.x;
+    if (c < n_out) load(c);
+    for (; c < n_out; c += gridDim.x) {
+        int cnt = (int)min(chunk, n_in - c * chunk);
 #pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-            const int i = ib + u * (int)blockDim.x;
+        for (int u = 0; u < kRemPer; ++u) {
+            const int i = (int)threadIdx.x + u * kRemThreads;
             if (i < cnt) buf[0][i] = v[u];
         }
-    }
-    __syncthreads();
-    int cur = 0;
-    for (int l = 0; l < q; ++l) {
-        const int m = (cnt + 4) / 5;
-        for (int i = threadIdx.x; i < m; i += blockDim.x)
-            buf[cur ^ 1][i] = lower_median_small(&buf[cur][5 * i], min(5, cnt - 5 * i));
+        if (c + gridDim.x < n_out) load(c + gridDim.x);
         __syncthreads();
-        cur ^= 1;
-        cnt = m;
+        int cur = 0;
+        for (int l = 0; l < q; ++l) {
+            const int m = (cnt + 4) / 5;
+            for (int i = threadIdx.x; i < m; i += blockDim.x)
+                buf[cur ^ 1][i] = lower_median_small(&buf[cur][5 * i], min(5, cnt - 5 * i));
+            __syncthreads();
+            cur ^= 1;
+            cnt = m;
+        }
+        if (threadIdx.x == 0) out[(int64_t)trial * out_pitch + c] = buf[cur][0];
+        __syncthreads();   // buf[0] is rewritten with the next chunk
     }
-    if (threadIdx.x == 0) out[(int64_t)trial * out_pitch + blockIdx.x] = buf[cur][0];
 }
 
 // ------------------------------------------------------- baseline walkers
 // Exact baseline b(t) evaluated at consecutive samples t, t+1, ...
 
-struct MedianWalker {
+// The median baseline interpolates linearly between knots P samples apart:
+// within an interval b(t) = m_j + floor(delta (t - c_j) / P), kept as the
+// quotient q and remainder r of that division and advanced by the quotient
+// and remainder of delta / P per sample.  I is the integer type of the
+// per-sample state: int32 when P < 2^30 (then r + dr < 2P < 2^31, and q lies
+// between 0 and delta (P - 1) / P, inside int32 for series within +-2^30),
+// int64 otherwise; the set-up is 64-bit either way.
+template <typename I>
+struct MedianWalkerT {
     const int32_t* m;
     int64_t M, P, half;
-    int64_t t, next, base, q, r, dq, dr;
+    int64_t next;          // the sample at which the walker is set up again
+    I base, q, r, dq, dr, PI;
+    int32_t left;          // samples until then
     bool interior;
 
-    __device__ void init(int64_t t_) {
-        t = t_;
+    __device__ void init(int64_t t) {
         const int64_t c_last = P * (M - 1) + half;
+        int64_t nx;
+        PI = (I)P;
         if (M == 1 || t <= half) {
-            base = m[0]; q = 0; interior = false;
-            next = (M == 1) ? LLONG_MAX : half + 1;
-            return;
+            base = m[0]; q = 0; r = 0; interior = false;
+            nx = (M == 1) ? LLONG_MAX : half + 1;
+        } else if (t >= c_last) {
+            base = m[M - 1]; q = 0; r = 0; interior = false;
+            nx = LLONG_MAX;
+        } else {
+            const int64_t j = (t - half) / P;
+            const int64_t cj = P * j + half;
+            const int64_t delta = (int64_t)m[j + 1] - (int64_t)m[j];
+            const int64_t num = delta * (t - cj);
+            const int64_t q64 = floor_div_pos(num, P);
+            const int64_t dq64 = floor_div_pos(delta, P);
+            q = (I)q64;
+            r = (I)(num - q64 * P);
+            dq = (I)dq64;
+            dr = (I)(delta - dq64 * P);
+            base = m[j];
+            interior = true;
+            nx = cj + P;
         }
-        if (t >= c_last) {
-            base = m[M - 1]; q = 0; interior = false; next = LLONG_MAX;
-            return;
-        }
-        const int64_t j = (t - half) / P;
-        const int64_t cj = P * j + half;
-        const int64_t delta = (int64_t)m[j + 1] - (int64_t)m[j];
-        const int64_t num = delta * (t - cj);
-        q = floor_div_pos(num, P);
-        r = num - q * P;
-        dq = floor_div_pos(delta, P);
-        dr = delta - dq * P;
-        base = m[j];
-        interior = true;
-        next = cj + P;
+        next = nx;
+        left = (int32_t)min(nx - t, (int64_t)1 << 30);
     }
-    __device__ __forceinline__ int64_t value() const { return base + q; }
+    __device__ __forceinline__ int64_t value() const { return (int64_t)(base + q); }
     __device__ __forceinline__ void step() {
-        ++t;
-        if (t == next) { init(t); return; }
+        if (--left == 0) { init(next); return; }
         if (interior) {
             q += dq;
             r += dr;
-            if (r >= P) { r -= P; ++q; }
+            if (r >= PI) { r -= PI; ++q; }
         }
     }
 };
@@ -166,11 +192,20 @@ struct BaselineCtx {
     int64_t pre_pitch, H;
 };
 
-// Walker<0>: running-median baseline; Walker<1>: moving-mean baseline.  The
+// Walker<0> / Walker<2>: running-median baseline; Walker<1>: moving-mean baseline.  The
 // mode is uniform per launch, so the kernels are instantiated per mode.
 template <int MODE> struct Walker;
 
-template <> struct Walker<0> : MedianWalker {
+// median mode with knots less than 2^30 samples apart (every practical case)
+template <> struct Walker<0> : MedianWalkerT<int32_t> {
+    __device__ void setup(const BaselineCtx& c, const int32_t*, int64_t, int trial) {
+        m = c.knots + (int64_t)trial * c.knot_pitch;
+        M = c.M; P = c.P; half = c.half;
+    }
+};
+
+// median mode, knots 2^30 samples apart or more
+template <> struct Walker<2> : MedianWalkerT<int64_t> {
     __device__ void setup(const BaselineCtx& c, const int32_t*, int64_t, int trial) {
         m = c.knots + (int64_t)trial * c.knot_pitch;
         M = c.M; P = c.P; half = c.half;
@@ -1594,8 +1629,9 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
                 const int64_t out_pitch = which == 0 ? pitches[0] : pitches[1];
                 if (n_out > out_pitch) return cudaErrorInvalidValue;
                 ++*nlaunch;
-                remedian_pass_kernel<<<dim3((unsigned)n_out, ndm), 256, 0, s>>>(in, in_pitch, n_in, q,
-                                                                            out, out_pitch);
+                const int64_t gx = ceil_div(n_out, kRemChunksPerBlock);
+                remedian_pass_kernel<<<dim3((unsigned)gx, ndm), kRemThreads, 0, s>>>(
+                    in, in_pitch, n_in, q, out, out_pitch, n_out);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 in = out;
                 in_pitch = out_pitch;
@@ -1623,8 +1659,9 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
 
-    return a.baseline_mode == 0 ? launch_walkers<0>(a, bc, s, nlaunch)
-                                : launch_walkers<1>(a, bc, s, nlaunch);
+    if (a.baseline_mode != 0) return launch_walkers<1>(a, bc, s, nlaunch);
+    return bc.P < ((int64_t)1 << 30) ? launch_walkers<0>(a, bc, s, nlaunch)
+                                     : launch_walkers<2>(a, bc, s, nlaunch);
 }
 
 }  // namespace hp
