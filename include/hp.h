@@ -143,7 +143,7 @@ int hp_plan_destroy(hp_plan* plan);
  * that maximum).  hp_search, hp_dedisperse, hp_plan_autotune, batches (the
  * variant's files through their own two stages; hp_batch_autotune refuses it)
  * and streams (per searched buffer) follow the variant (tile shapes 7, 11,
- * 12, 14 and 19 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
+ * 12 and 14 only).  |e - delay| <= |a_c - a_top| |DM_n - DM_d| + 2, a_c the
  * delay of channel c per unit DM in samples. */
 #define HP_PARAM_SUBBAND_CHANS 12 /* S: channels per sub-band, 0 = direct dedispersion (default) */
 #define HP_PARAM_SUBBAND_GROUP 13 /* G: trials per group, 1..ndm (default 8) */
@@ -281,15 +281,18 @@ int hp_plan_autotune(hp_plan* plan, const uint8_t* filterbank_dev, int64_t nsamp
  * captured once into a CUDA graph and replayed while the inputs, sizes and
  * outputs stay the same.  Results are identical to hp_search per file.
  *   plans  host array of nfiles (1..HP_BATCH_MAX_FILES) caller-owned plans, one
- *          per file; they must outlive the batch, and the batch sets their
- *          dedispersion tile configuration (all files share one). */
+ *          per file; they must outlive the batch, and the batch sets the
+ *          dedispersion tile configuration of its direct-dedispersion files
+ *          (they share one: at creation the first such file's); files in the
+ *          sub-band variant keep their own stage-1 tile shape. */
 typedef struct hp_batch hp_batch;
 #define HP_BATCH_MAX_FILES 32
 
 int hp_batch_create(hp_batch** out, hp_plan* const* plans, int nfiles);
 int hp_batch_destroy(hp_batch* batch);
 
-/* Use tile configuration `config` for every file (drops a captured graph). */
+/* Use tile configuration `config` for every direct-dedispersion file (drops a
+ * captured graph). */
 int hp_batch_set_config(hp_batch* batch, int config);
 
 /* Time every dedispersion tile shape (the configurations that

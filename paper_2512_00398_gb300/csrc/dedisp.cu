@@ -717,7 +717,7 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
 }
 
 bool segmented_config(int cfg) {
-    return cfg == 7 || cfg == 11 || cfg == 12 || cfg == 14 || cfg == 19;
+    return cfg == 7 || cfg == 11 || cfg == 12 || cfg == 14;
 }
 
 cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& b, int* status,
@@ -729,7 +729,6 @@ cudaError_t launch_dedisp_segmented(int cfg, const DedispBatch& b, int* status,
         case 11: return run_dedisp_rows<2, 5, 12, 1, 4, 1, true>(b, sb, status, timeout_ns, s);
         case 12: return run_dedisp_rows<2, 7, 12, 1, 4, 2, true>(b, sb, status, timeout_ns, s);
         case 14: return run_dedisp_rows<1, 7, 24, 1, 4, 2, true>(b, sb, status, timeout_ns, s);
-        case 19: return run_dedisp_rows<1, 17, 15, 1, 3, 1, true>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -995,7 +995,7 @@ int batch_prepare(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         hp_plan* p = b->plans[i];
         int rc = validate_search_input(p, fbs ? fbs[i] : nullptr, nsamps[i]);
         if (rc) return rc;
-        p->dedisp_cfg = b->cfg;
+        if (p->sb_chans <= 0) p->dedisp_cfg = b->cfg;   // sub-band files keep their stage-1 shape
         rc = ensure_device_tables(p);
         if (rc) return rc;
         (*layouts)[i] = make_layout(p, nsamps[i], true);
@@ -1544,7 +1544,10 @@ int hp_batch_create(hp_batch** out, hp_plan* const* plans, int nfiles) {
     hp_batch* b = new (std::nothrow) hp_batch;
     if (!b) return HP_ERR_OOM;
     b->plans.assign(plans, plans + nfiles);
-    b->cfg = plans[0]->dedisp_cfg;
+    // the direct files' tile shape: the first direct file's (sub-band files keep theirs)
+    b->cfg = kDefaultDedispConfig;
+    for (int i = nfiles - 1; i >= 0; --i)
+        if (plans[i]->sb_chans <= 0) b->cfg = plans[i]->dedisp_cfg;
     int rc = HP_OK;
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) rc = HP_ERR_CUDA;
     for (int i = 0; i < nfiles && !rc; ++i) {
@@ -1687,7 +1690,7 @@ int hp_batch_autotune(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsa
     batch_drop_graph(b);
     if (rc) return rc;
     for (hp_plan* p : b->plans) {
-        p->dedisp_cfg = b->cfg;
+        if (p->sb_chans <= 0) p->dedisp_cfg = b->cfg;
         rc = ensure_device_tables(p);
         if (rc) return rc;
     }

@@ -15,7 +15,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 SNR_TOL = 1e-4
-SEGMENTED = [7, 11, 12, 14, 19]
+SEGMENTED = [7, 11, 12, 14]
 
 
 @pytest.fixture(scope="module")
