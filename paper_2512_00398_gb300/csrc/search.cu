@@ -17,6 +17,7 @@
 //             integer compare); one candidate per maximal run, at the largest
 //             S (first on ties), appended with an atomic counter.
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kHistThreads, 4) mad_hist_kernel(const int32_t
                                                                 int32_t* Y, int64_t ypitch,
                                                                 int yvec) {
     __shared__ uint32_t h[kHistBins];
+    __shared__ __align__(16) int4 tile[kHistThreads / 32][32 * kHistStep / 4];
     const int trial = blockIdx.y;
     for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -319,7 +321,65 @@ __global__ void __launch_bounds__(kHistThreads, 4) mad_hist_kernel(const int32_t
     // first sample of step 0 and the distance between steps
     const int64_t s_first = blk0 + (int64_t)threadIdx.x * kHistSpan;
     constexpr int64_t stride = kHistStep;
-    if (s_first < n) {
+    if (vec && yvec && blk0 + kHistBlock <= n) {
+        // Whole block, aligned rows: a warp moves the step's 32 pieces of 16
+        // samples (one per lane, 1 KB apart) through shared memory, eight whole
+        // 64-byte pieces per load or store instruction; lane l then reads its own
+        // piece.  16-byte slot of (piece p, quarter c): 4p + (c ^ ((p >> 1) & 3)),
+        // so that both the eight lanes of a cooperative access (pieces p, p + 1,
+        // quarters 0-3) and eight lanes reading their own pieces (p .. p + 7, one
+        // quarter) touch eight distinct 16-byte bank groups.
+        const int lane = threadIdx.x & 31;
+        int4* T = tile[threadIdx.x >> 5];
+        const int64_t wbase = blk0 + (int64_t)(threadIdx.x & ~31) * kHistSpan;
+        auto slot = [](int p, int c) { return 4 * p + (c ^ ((p >> 1) & 3)); };
+        int4 g[4];
+        auto gload = [&](int j) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int p = (lane >> 2) + 8 * k, c = lane & 3;
+                g[k] = __ldg(reinterpret_cast<const int4*>(row + wbase + (int64_t)p * kHistSpan +
+                                                           j * kHistStep) + c);
+            }
+        };
+        Walker<MODE> w;
+        w.setup(bc, row, n, trial);
+        w.init(s_first);
+        gload(0);
+        for (int j = 0; j < kHistSpan / kHistStep; ++j) {
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) T[slot((lane >> 2) + 8 * k, lane & 3)] = g[k];
+            __syncwarp();
+            if (j + 1 < kHistSpan / kHistStep) gload(j + 1);
+            int32_t v[kHistStep];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int4 x = T[slot(lane, c)];
+                v[4 * c] = x.x; v[4 * c + 1] = x.y; v[4 * c + 2] = x.z; v[4 * c + 3] = x.w;
+            }
+#pragma unroll
+            for (int q = 0; q < kHistStep; ++q) {
+                const int32_t y = (int32_t)((int64_t)v[q] - w.value());
+                v[q] = y;
+                const uint32_t m = y < 0 ? 0u - (uint32_t)y : (uint32_t)y;
+                atomicAdd(&h[m < (uint32_t)kHistFine ? (int)m
+                                                     : kHistFine + (int)min(m >> 12, (uint32_t)(kHistFine - 1))],
+                          1u);
+                w.step();
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                T[slot(lane, c)] = make_int4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int p = (lane >> 2) + 8 * k, c = lane & 3;
+                reinterpret_cast<int4*>(yrow + wbase + (int64_t)p * kHistSpan + j * kHistStep)[c] =
+                    T[slot(p, c)];
+            }
+        }
+    } else if (s_first < n) {
         Walker<MODE> w;
         w.setup(bc, row, n, trial);
         w.init(s_first);
@@ -881,6 +941,7 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
     __shared__ int32_t width_s[kMaxWidths];
     __shared__ int2 wt_s[kMaxWidths];               // {W, threshold} of the widths that can fire:
     __shared__ int nlive, nexact;                   // [0, nexact) tested exactly, the rest by group bound
+    __shared__ int32_t thr_p2[4];                   // widths 1, 2, 4, 8 (INT32_MAX: not searched)
     const int trial = blockIdx.y;
     if (!narrow_trial(a, trial)) return;             // detect_kernel takes the trial
     const int64_t n = a.nout;
@@ -901,12 +962,18 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
         width_s[tid] = a.widths[tid];
     }
     if (tid == 0) {
+        // widths 1, 2, 4, 8 apart (tested from registers with fixed shifts), then
+        // the other widths below 16 or not multiples of 16, then the multiples of 16
+        for (int j = 0; j < 4; ++j) thr_p2[j] = INT32_MAX;
         int m = 0;
         for (int pass = 0; pass < 2; ++pass) {
             for (int k = 0; k < a.nw; ++k) {
                 const int64_t tk = a.tint[(int64_t)trial * a.nw + k];
-                if (tk < (int64_t)INT32_MAX && ((a.widths[k] & 15) == 0) == (pass == 1))
-                    wt_s[m++] = make_int2(a.widths[k], (int)tk);
+                const int W = a.widths[k];
+                if (tk >= (int64_t)INT32_MAX) continue;
+                const bool p2 = W == 1 || W == 2 || W == 4 || W == 8;
+                if (pass == 0 && p2) thr_p2[31 - __clz(W)] = (int32_t)tk;
+                else if (!p2 && ((W & 15) == 0) == (pass == 1)) wt_s[m++] = make_int2(W, (int)tk);
             }
             if (pass == 0) nexact = m;
         }
@@ -1006,6 +1073,25 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
         const bool full = t0 + kDWChunk - 1 <= tmax && t0 + kDWChunk - 1 <= n - a.wmax;
         if (full) {
             const int nl = nlive, ne = nexact;
+            // widths 1, 2, 4, 8: the sums W ahead are this thread's own entries
+            auto test_p2 = [&](auto wc) {
+                constexpr int W = decltype(wc)::value;
+                constexpr int j = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3;
+                const uint32_t thr = (uint32_t)thr_p2[j];
+                if (thr == (uint32_t)INT32_MAX) return;
+                uint32_t acc = 0xffffffffu;
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) {
+                    const uint32_t q0 = i + W < 16 ? p[i + W] : nx[i + W - 16];
+                    const uint32_t q1 = i + 1 + W < 16 ? p[i + 1 + W] : nx[i + 1 + W - 16];
+                    acc &= (q0 - p[i] - thr) & (q1 - p[i + 1] - thr);
+                }
+                if ((int32_t)acc >= 0) hit = 1u;
+            };
+            test_p2(std::integral_constant<int, 1>{});
+            test_p2(std::integral_constant<int, 2>{});
+            test_p2(std::integral_constant<int, 4>{});
+            test_p2(std::integral_constant<int, 8>{});
             for (int k = 0; k < ne; ++k) {
                 const int2 wt = wt_s[k];
                 const uint32_t thr = (uint32_t)wt.y;
