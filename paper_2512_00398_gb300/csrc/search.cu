@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(kRemThreads) remedian_pass_kernel(const int32_
         }
         if (c + gridDim.x < n_out) load(c + gridDim.x);
         __syncthreads();
-        int cur = 0;
-        for (int l = 0; l < q; ++l) {
+        int cur = 0, l = 0;
+        // levels with more than 32 medians: the whole block, a barrier each
+        for (; l < q && cnt > 160; ++l) {
             const int m = (cnt + 4) / 5;
             for (int i = threadIdx.x; i < m; i += blockDim.x)
                 buf[cur ^ 1][i] = lower_median_small(&buf[cur][5 * i], min(5, cnt - 5 * i));
@@ -95,8 +96,20 @@ __global__ void __launch_bounds__(kRemThreads) remedian_pass_kernel(const int32_
             cur ^= 1;
             cnt = m;
         }
-        if (threadIdx.x == 0) out[(int64_t)trial * out_pitch + c] = buf[cur][0];
-        __syncthreads();   // buf[0] is rewritten with the next chunk
+        // the rest (at most 32 medians per level) in the first warp
+        if (threadIdx.x < 32) {
+            for (; l < q; ++l) {
+                const int m = (cnt + 4) / 5;
+                if ((int)threadIdx.x < m)
+                    buf[cur ^ 1][threadIdx.x] =
+                        lower_median_small(&buf[cur][5 * threadIdx.x], min(5, cnt - 5 * (int)threadIdx.x));
+                __syncwarp();
+                cur ^= 1;
+                cnt = m;
+            }
+            if (threadIdx.x == 0) out[(int64_t)trial * out_pitch + c] = buf[cur][0];
+        }
+        __syncthreads();   // buf is rewritten with the next chunk
     }
 }
 
@@ -876,7 +889,10 @@ constexpr int kDWPer = 16;                          // consecutive starts per th
 constexpr int kDWChunk = kDWThreads * kDWPer;       // starts per chunk
 constexpr int kDWLead = 16;                         // prefix entries before a segment's first start
 
-__device__ __forceinline__ uint32_t block_exclusive_scan32(uint32_t v, uint32_t* warp_tot) {
+// Exclusive prefix of v over the block's threads, and in *total the block's
+// sum; one barrier: every warp adds up the warp totals before it itself.
+__device__ __forceinline__ uint32_t block_exclusive_scan32(uint32_t v, uint32_t* warp_tot,
+                                                           uint32_t* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -886,17 +902,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan32(uint32_t v, uint32_t*
     }
     if (lane == 31) warp_tot[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+    uint32_t before = 0, all = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += u;
-        }
-        warp_tot[lane] = w;
+    for (int i = 0; i < kDWThreads / 32; ++i) {
+        const uint32_t t = warp_tot[i];
+        before += i < warp ? t : 0u;
+        all += t;
     }
-    __syncthreads();
-    return x - v + (warp > 0 ? warp_tot[warp - 1] : 0u);
+    *total = all;
+    return x - v + before;
 }
 
 // q[i] = the prefix entry W after p[i], for W up to 16: from this thread's own
@@ -1016,14 +1030,15 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
             mx = __vimax3_s32(mx, x0, x1);
             mn = __vimin3_s32(mn, x0, x1);
         }
-        const uint32_t off = carry + block_exclusive_scan32(run, warp_tot);
+        uint32_t chunk_total;
+        const uint32_t off = carry + block_exclusive_scan32(run, warp_tot, &chunk_total);
 #pragma unroll
         for (int e = 0; e < 16; ++e) ex[e] += off;
         const int pos = (int)((f + kDWPer * tid) & R.mask);
         R.put16(pos, ex);
         gpm[pos >> 4] = make_uint2(off, (uint32_t)mx);
         gmn[pos >> 4] = mn;
-        carry += warp_tot[kDWThreads / 32 - 1];
+        carry += chunk_total;
         __syncthreads();   // ring entries visible; warp_tot free for the next scan
     };
     // entries [0, f0) before the first chunk: the chunk, the lead and the widest boxcar
