@@ -325,6 +325,8 @@ struct MergeArgs {
     int32_t* scan;             // [cap]
     int32_t* block_sums;       // [cap / 1024 + 1]
     int64_t* n_clamped;        // one int64
+    int64_t* trial_start;      // [ndm + 1]: first sorted entry of each trial, or null
+    int ndm;                   // trials (rows of trial_start - 1)
     hp_cand* out;
     int64_t out_cap;
     int64_t* out_count;

@@ -163,6 +163,14 @@ __device__ __forceinline__ int64_t lower_bound_key(const uint64_t* k, int64_t n,
     return lo;
 }
 
+// trial_start[d] = the first sorted entry of trial d or later (d = ndm: n)
+__global__ void trial_start_kernel(MergeArgs a, const uint64_t* __restrict__ keys) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d > a.ndm) return;
+    const int64_t n = *a.n_clamped;
+    a.trial_start[d] = d == a.ndm ? n : lower_bound_key(keys, n, (uint64_t)d << kKeyDmShift);
+}
+
 __global__ void link_kernel(MergeArgs a, const uint64_t* __restrict__ keys) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = *a.n_clamped;
@@ -174,14 +182,28 @@ __global__ void link_kernel(MergeArgs a, const uint64_t* __restrict__ keys) {
     const int64_t t_first = ti - (int64_t)a.wmax - a.t_gap;
     const int64_t t_last = ei + a.t_gap;
     for (int dd = di; dd <= di + a.dm_tol; ++dd) {
-        const uint64_t lo_key = ((uint64_t)dd << kKeyDmShift) |
-                                ((uint64_t)(t_first > 0 ? t_first : 0) << kKeySampleShift);
-        for (int64_t j = lower_bound_key(keys, n, lo_key); j < n; ++j) {
+        // the friends j > i: in i's own trial the entries after i, in a later
+        // trial from the first entry at t_first (searched within that trial's
+        // entries when the per-trial table is there)
+        int64_t j0;
+        if (dd == di) {
+            j0 = i + 1;
+        } else {
+            const uint64_t lo_key = ((uint64_t)dd << kKeyDmShift) |
+                                    ((uint64_t)(t_first > 0 ? t_first : 0) << kKeySampleShift);
+            if (a.trial_start) {
+                if (dd >= a.ndm) break;
+                const int64_t b0 = a.trial_start[dd], b1 = a.trial_start[dd + 1];
+                j0 = b0 + lower_bound_key(keys + b0, b1 - b0, lo_key);
+            } else {
+                j0 = lower_bound_key(keys, n, lo_key);
+            }
+        }
+        for (int64_t j = j0; j < n; ++j) {
             const uint64_t kj = keys[j];
             if (key_dm(kj) != dd) break;
             const int64_t tj = key_sample(kj);
             if (tj > t_last) break;
-            if (dd == di && j <= i) continue;
             const int wj = key_width(kj);
             if (abs(wi - wj) > a.w_tol) continue;
             const int64_t ej = tj + a.widths[wj];
@@ -352,6 +374,10 @@ cudaError_t launch_merge(const MergeArgs& a_in, cudaStream_t s, int64_t* nlaunch
     const int64_t* vals = a.vals[cur];
     ++*nlaunch;
     uf_init_kernel<<<g256, 256, 0, s>>>(a);
+    if (a.trial_start) {
+        ++*nlaunch;
+        trial_start_kernel<<<(unsigned)ceil_div((int64_t)a.ndm + 1, 256), 256, 0, s>>>(a, keys);
+    }
     ++*nlaunch;
     link_kernel<<<g256, 256, 0, s>>>(a, keys);
     ++*nlaunch;

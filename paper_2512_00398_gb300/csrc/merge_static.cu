@@ -139,6 +139,8 @@ extern "C" int hp_merge_static(const hp_raw_cand* raw_dev, const int64_t* nraw_d
     m.scan = reinterpret_cast<int32_t*>(base + kOffScan);
     m.block_sums = reinterpret_cast<int32_t*>(base + kOffBlockSums);
     m.n_clamped = reinterpret_cast<int64_t*>(base + kOffNClamped);
+    m.trial_start = nullptr;   // friends found by search over the whole sorted list
+    m.ndm = 0;
     m.out = cand_out->data;
     m.out_cap = cand_out->capacity;
     m.out_count = cand_out->count;

@@ -547,6 +547,7 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
     L.scan = take(cap * 4);
     L.bsums = take((cap / 1024 + 2) * 4);
     L.nclamp = take(8);
+    L.tstart = take(((int64_t)p->ndm() + 1) * 8);
     L.total = off;
     return L;
 }
@@ -920,6 +921,8 @@ MergeArgs make_merge_args(hp_plan* p, const Layout& L, uint8_t* ws, const hp_raw
     m.scan = (int32_t*)(ws + L.scan);
     m.block_sums = (int32_t*)(ws + L.bsums);
     m.n_clamped = (int64_t*)(ws + L.nclamp);
+    m.trial_start = (int64_t*)(ws + L.tstart);
+    m.ndm = p->ndm();
     m.out = out->data;
     m.out_cap = out->capacity;
     m.out_count = out->count;

@@ -21,7 +21,8 @@ struct Layout {
     size_t xt = 0, D = 0, lvl_a = 0, lvl_b = 0, mean = 0, hist = 0, rbucket = 0, rrank = 0,
            mad = 0, ybound = 0, sigma = 0, tint = 0, raw = 0, raw_count = 0, keys0 = 0, keys1 = 0,
            vals0 = 0, vals1 = 0, parent = 0, best = 0, rep = 0, members = 0, dmlo = 0,
-           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0;
+           dmhi = 0, tlo = 0, thi = 0, scan = 0, bsums = 0, nclamp = 0, tails = 0, tcount = 0,
+           tstart = 0;
     // RFI stage: channel counts, statistics and flags, the zero-DM series and
     // the scratch of its statistics (a one-trial stats-only search)
     size_t r_hist = 0, r_med = 0, r_spread = 0, r_cflag = 0, r_sflag = 0, r_one = 0, r_z = 0,

@@ -1259,11 +1259,15 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
     }
 }
 
-// Runs that leave the detect tile's halo: continue each one sample at a time
-// from the dedispersed row with exact baseline walkers, then emit it.
-// A warp per run, 32 starts per step: S(v) = S(v - 1) - y(v - 1) + y(v - 1 + W),
-// so the step's sums are S(u - 1) plus a warp prefix sum of those differences;
-// the run ends at the first start below threshold (or past the last start).
+// Runs that leave the detect tile's halo or the ring: continue each one from
+// y in global memory, then emit it.  A warp per run, 128 starts per step (4
+// consecutive per lane): S(v) = S(v - 1) - y(v - 1) + y(v - 1 + W), so the
+// step's sums are S(u - 1) plus a lane-local then warp prefix sum of those
+// differences; the run ends at the first start below threshold (or past the
+// last start), and its candidate is the largest S before that (ties: the
+// earliest start).
+constexpr int kTailPer = 4;
+
 __global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
     const int64_t cnt = min(*a.tail_count, a.tail_cap);
     const int lane = threadIdx.x & 31;
@@ -1276,19 +1280,34 @@ __global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
         const int64_t last = n - W;
         const int64_t thr = a.tint[(int64_t)r.trial * a.nw + r.k];
         int64_t best_S = r.best_S, best_t = r.best_t, Sp = r.S_prev;
-        for (int64_t v0 = r.u; v0 <= last; v0 += 32) {
-            const int64_t v = v0 + lane;
-            const bool inr = v <= last;
-            int64_t d = inr ? (int64_t)__ldg(yrow + v - 1 + W) - (int64_t)__ldg(yrow + v - 1) : 0;
+        for (int64_t v0 = r.u; v0 <= last; v0 += 32 * kTailPer) {
+            const int64_t vb = v0 + kTailPer * lane;
+            int64_t c[kTailPer];
+            int64_t run = 0;
+#pragma unroll
+            for (int e = 0; e < kTailPer; ++e) {
+                const int64_t v = vb + e;
+                if (v <= last) run += (int64_t)__ldg(yrow + v - 1 + W) - (int64_t)__ldg(yrow + v - 1);
+                c[e] = run;                                  // inclusive, lane-local
+            }
+            int64_t x = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, d, o);
-                if (lane >= o) d += u;
+                const int64_t u = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += u;
             }
-            const int64_t Sv = Sp + d;
-            const unsigned stop = __ballot_sync(0xffffffffu, !(inr && Sv >= thr));
-            const int first = stop ? __ffs(stop) - 1 : 32;
-            int64_t cs = lane < first ? Sv : LLONG_MIN, ct = v;
+            const int64_t before = Sp + x - run;             // S(vb - 1)
+            int lane_first = kTailPer;                       // first start below threshold
+#pragma unroll
+            for (int e = kTailPer - 1; e >= 0; --e)
+                if (!(vb + e <= last && before + c[e] >= thr)) lane_first = e;
+            const unsigned stop = __ballot_sync(0xffffffffu, lane_first < kTailPer);
+            const int first_lane = stop ? __ffs(stop) - 1 : 32;
+            const int lim = lane < first_lane ? kTailPer : (lane == first_lane ? lane_first : 0);
+            int64_t cs = LLONG_MIN, ct = vb;
+#pragma unroll
+            for (int e = 0; e < kTailPer; ++e)
+                if (e < lim && before + c[e] > cs) { cs = before + c[e]; ct = vb + e; }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const int64_t os = __shfl_down_sync(0xffffffffu, cs, o);
@@ -1299,7 +1318,7 @@ __global__ void tail_kernel(const __grid_constant__ SearchArgs a) {
             ct = __shfl_sync(0xffffffffu, ct, 0);
             if (cs > best_S) { best_S = cs; best_t = ct; }
             if (stop) break;
-            Sp = __shfl_sync(0xffffffffu, Sv, 31);
+            Sp += __shfl_sync(0xffffffffu, x, 31);
         }
         if (lane == 0) emit(a, r.trial, r.k, best_t, best_S);
     }
@@ -1624,7 +1643,7 @@ cudaError_t launch_detect(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
     detect32_kernel<<<dgrid32, kDWThreads, smem32, s>>>(a, seg, ring);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nlaunch;
-    tail_kernel<<<256, 128, 0, s>>>(a);
+    tail_kernel<<<2048, 128, 0, s>>>(a);   // a warp per run; idle warps leave at once
     return cudaGetLastError();
 }
 
