@@ -674,6 +674,55 @@ __device__ __forceinline__ bool follow_run(int64_t ts, int64_t last, int64_t bas
     return tail;
 }
 
+// follow_run for sums that fit int32 (the 32-bit detection): 4 consecutive
+// starts per lane, 128 per warp step, the running maximum in 32 bits.
+template <class BoxcarFn>
+__device__ __forceinline__ bool follow_run32(int64_t ts, int64_t last, int64_t base, int64_t len,
+                                             int64_t W, int32_t thr, BoxcarFn boxcar, int lane,
+                                             int64_t* best_S_out, int64_t* best_t_out,
+                                             int64_t* tail_u) {
+    int32_t best_S = INT32_MIN;
+    int64_t best_t = ts;
+    bool tail = false;
+    for (int64_t u0 = ts;; u0 += 128) {
+        const int64_t ub = u0 + 4 * lane;
+        int32_t Sv[4];
+        int lane_first = 4;                      // first of this lane's starts not above
+#pragma unroll
+        for (int e = 3; e >= 0; --e) {
+            const int64_t u = ub + e;
+            const bool inr = u <= last && u - base + W <= len;
+            Sv[e] = inr ? boxcar(u) : 0;
+            if (!(inr && Sv[e] >= thr)) lane_first = e;
+        }
+        const unsigned stop = __ballot_sync(0xffffffffu, lane_first < 4);
+        const int first_lane = stop ? __ffs(stop) - 1 : 32;
+        const int lim = lane < first_lane ? 4 : (lane == first_lane ? lane_first : 0);
+        int32_t cs = INT32_MIN;
+        int ct = 4 * lane;                       // start offset from u0
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < lim && Sv[e] > cs) { cs = Sv[e]; ct = 4 * lane + e; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int32_t os = __shfl_down_sync(0xffffffffu, cs, o);
+            const int ot = __shfl_down_sync(0xffffffffu, ct, o);
+            if (os > cs || (os == cs && ot < ct)) { cs = os; ct = ot; }
+        }
+        cs = __shfl_sync(0xffffffffu, cs, 0);
+        ct = __shfl_sync(0xffffffffu, ct, 0);
+        if (cs > best_S) { best_S = cs; best_t = u0 + ct; }
+        if (!stop) continue;
+        const int64_t ue = u0 + 4 * first_lane + __shfl_sync(0xffffffffu, lane_first, first_lane);
+        tail = ue <= last && ue - base + W > len;
+        *tail_u = ue;
+        break;
+    }
+    *best_S_out = best_S;
+    *best_t_out = best_t;
+    return tail;
+}
+
 // One tile of starts of one trial with an int64 prefix (the trials that
 // detect32_kernel cannot take).
 __device__ void detect_tile(const SearchArgs& a, int trial, int64_t tile) {
@@ -1213,7 +1262,7 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
                 unsigned lanes = __ballot_sync(0xffffffffu, starts != 0);
                 auto box32 = [&](int64_t u) {
                     const int64_t i = u - base;
-                    return (int64_t)(int32_t)(R.get(i + W) - R.get(i));
+                    return (int32_t)(R.get(i + W) - R.get(i));
                 };
                 while (lanes) {
                     const int L = __ffs(lanes) - 1;
@@ -1224,8 +1273,8 @@ __global__ void __launch_bounds__(kDWThreads) detect32_kernel(const __grid_const
                         const int e = __ffs(sL) - 1;
                         sL &= sL - 1;
                         int64_t bS, bt, tu = 0;
-                        const bool tail = follow_run(tL + e, last, base, len, (int64_t)W,
-                                                     (int64_t)thr, box32, lane, &bS, &bt, &tu);
+                        const bool tail = follow_run32(tL + e, last, base, len, (int64_t)W,
+                                                       thr, box32, lane, &bS, &bt, &tu);
                         if (lane == 0) {
                             if (!tail) {
                                 emit(a, trial, k, bt, bS);
