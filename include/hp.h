@@ -256,7 +256,9 @@ int hp_width_sigmas(hp_plan* plan, double* sigma_w_dev, int64_t* mad_w_dev, void
 
 /* Candidate merging and clustering (Section II-B; Algorithm 1, last stage):
  *   raw_dev / nraw_dev  device raw candidates and their device count (as
- *                       written by hp_detect; entries beyond capacity ignored)
+ *                       written by hp_detect: dm_idx < the plan's trial count,
+ *                       width_idx < its width count; entries beyond capacity
+ *                       ignored)
  *   sigma_dev           device double [ndm], per-trial sigma from hp_detect
  *   cand_out            merged clusters (see hp_cand_buf) */
 int hp_merge(hp_plan* plan, const hp_raw_cand* raw_dev, const int64_t* nraw_dev,
