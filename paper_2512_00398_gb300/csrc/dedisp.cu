@@ -54,14 +54,16 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
 
 namespace {
 
-constexpr int kTC = 64;    // channels per transpose tile
-constexpr int kTS = 256;   // samples per transpose tile (4 rows of 64 per thread)
+constexpr int kTC = 128;   // channels per transpose tile (whole 128-byte lines of a row)
+constexpr int kTS = 256;   // samples per transpose tile
 
-// One 256 x 64 byte tile of the transpose: rows t0.., channels c0.. of x
+// One 256 x 128 byte tile of the transpose: rows t0.., channels c0.. of x
 // [nsamps][nch] -> xt [nch][pitch] (zero beyond nsamps).  With ring_len > 0
 // row t is absolute sample a0 + t of a ring of ring_slots slots of ring_len
-// rows (a streamed beam's recent gulps).  Each thread has four 16-byte loads
-// in flight and writes four 16-byte pieces of one channel row.
+// rows (a streamed beam's recent gulps).  Reading, eight lanes take one row's
+// 128 bytes (each thread has eight 16-byte loads in flight); writing, the lanes
+// of a warp take 32 consecutive channels and write 16 samples of each per
+// step, half of the warps the even and half the odd 16-sample pieces.
 __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, int64_t nsamps,
                                                int nch, int vec, uint8_t* __restrict__ xt,
                                                int64_t pitch, int64_t t0, int c0,
@@ -69,12 +71,13 @@ __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, in
                                                int ring_slots = 1) {
     __shared__ __align__(16) uint8_t tile[kTS][kTC + 16];
     const int tid = threadIdx.x;
-    const int seg = tid & 3;
     {
-        uint4 q[kTS / 64];
+        constexpr int kSegs = kTC / 16, kRowsPer = 256 / kSegs;
+        const int seg = tid % kSegs;
+        uint4 q[kTS / kRowsPer];
 #pragma unroll
-        for (int r = 0; r < kTS / 64; ++r) {
-            const int row = (tid >> 2) + 64 * r;
+        for (int r = 0; r < kTS / kRowsPer; ++r) {
+            const int row = tid / kSegs + kRowsPer * r;
             const int64_t t = t0 + row;
             const int c = c0 + seg * 16;
             q[r] = make_uint4(0, 0, 0, 0);
@@ -96,16 +99,18 @@ __device__ __forceinline__ void transpose_tile(const uint8_t* __restrict__ x, in
             }
         }
 #pragma unroll
-        for (int r = 0; r < kTS / 64; ++r)
-            *reinterpret_cast<uint4*>(&tile[(tid >> 2) + 64 * r][seg * 16]) = q[r];
+        for (int r = 0; r < kTS / kRowsPer; ++r)
+            *reinterpret_cast<uint4*>(&tile[tid / kSegs + kRowsPer * r][seg * 16]) = q[r];
     }
     __syncthreads();
     {
-        const int cr = tid >> 2;
+        const int warp = tid >> 5;
+        const int cr = (warp % (kTC / 32)) * 32 + (tid & 31);
+        const int half = warp / (kTC / 32);               // even or odd pieces
         const int c = c0 + cr;
 #pragma unroll
-        for (int r = 0; r < kTS / 64; ++r) {
-            const int row0 = (4 * r + seg) * 16;
+        for (int k = 0; k < kTS / 32; ++k) {
+            const int row0 = (2 * k + half) * 16;
             const int64_t t = t0 + row0;
             if (c < nch && t < pitch) {
                 uint8_t v[16];
