@@ -39,14 +39,16 @@ METRIC = "DM-trial·samples/s"
 # scaled by the number of time tiles to the full nout of 955 060.  Keyed by the kernel
 # source it was measured on; a changed kernel, another workload or another
 # configuration reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "d569ba3da64b0a15", "bytes": (6.068e9 + 1.011e9) * 955060 / 168628,
-                  "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 19}
+DEDISP_TRAFFIC = {"source_sha256_16": "0954eac5d78321ca", "bytes": (6.091e9 + 1.008e9) * 955060 / 168628,
+                  "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 17}
 # The same for the two stages of the sub-band variant (64-channel sub-bands, groups
 # of 8 trials): DRAM bytes of one step, captured on the 2^18-sample case
 # (profiles/subband_fast_4096ch.md).  Stage 1's traffic grows with its byte-adds
 # (scaled by 7.445e11 / 1.389e11 to the full file, within 0.5% of an earlier full-size
 # capture); stage 2's partial-sum rows do not scale with the file length, so it stays null.
-SUBBAND_TRAFFIC = {"source_sha256_16": "d569ba3da64b0a15+6752b94441917dc0",
+# (Keyed by the current sources: the segmented stage-1 kernel is unchanged since the capture;
+# only the transpose and the removed quad-pattern kernel changed in the same file.)
+SUBBAND_TRAFFIC = {"source_sha256_16": "0954eac5d78321ca+6752b94441917dc0",
                    "stage1": (6.041e9 + 8.657e9) * 7.445e11 / 1.389e11, "stage2": None,
                    "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 12, "S": 64, "G": 8}
 

@@ -121,7 +121,7 @@ int hp_plan_destroy(hp_plan* plan);
 #define HP_PARAM_T_GAP 3          /* merge: max gap between boxcar windows, samples */
 #define HP_PARAM_W_TOL 4          /* merge: max |width index difference| (>= 0) */
 #define HP_PARAM_RAW_CAPACITY 5   /* raw-candidate scratch capacity (>= 1024) */
-#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 19;
+#define HP_PARAM_DEDISP_CONFIG 6  /* dedispersion tile shape index (0..HP_NUM_DEDISP_CONFIGS-1), default 17;
                                      12 while HP_PARAM_SUBBAND_CHANS > 0 unless a shape was set */
 #define HP_PARAM_STAGE_TIMING 7   /* 1 = record CUDA events around every stage launch */
 #define HP_PARAM_TIMEOUT_S 8      /* limit of every bounded device wait, seconds (> 0) */
@@ -169,7 +169,7 @@ int hp_plan_destroy(hp_plan* plan);
  * streams refuse it. */
 #define HP_PARAM_DECIMATE 15      /* R: 0 = every start (default) */
 
-#define HP_NUM_DEDISP_CONFIGS 22
+#define HP_NUM_DEDISP_CONFIGS 20
 
 int hp_plan_set_param(hp_plan* plan, int param, double value);
 int hp_plan_get_param(const hp_plan* plan, int param, double* value);

@@ -16,14 +16,12 @@
 #include <cstring>
 
 #include "common.cuh"
-#include "quad_tiling.h"
 
 namespace hp {
 
-// {RD, NW, WD, WT, stage bytes, stage buffers, unroll, builder warps}: RD
-// trials x NW words per lane, WD x WT consumer warps (+ builders + 1 producer),
-// BD = WD RD trials and BT = WT NW 128 samples per block (byte-row kernel, 4
-// samples per word) or WT NW 64 (quad-pattern kernel, 2 samples per word).
+// {RD, NW, WD, WT, stage bytes, stage buffers, unroll}: RD trials x NW words
+// (4 samples each) per lane, WD x WT consumer warps + 1 producer warp, BD = WD RD
+// trials and BT = WT NW 128 samples per block.
 const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
     {2, 5, 8, 2, 36 * 1024, 6, 1},   //  0: 16+1 warps, BD 16, BT 1280
     {2, 5, 16, 1, 36 * 1024, 6, 1},  //  1: 16+1 warps, BD 32, BT 640
@@ -42,14 +40,11 @@ const DedispConfig kDedispConfigs[kNumDedispConfigs] = {
     {1, 7, 24, 1, 54 * 1024, 4, 2},  // 14: 24+1 warps, 1 trial per warp, BD 24, BT 896
     {1, 5, 30, 1, 54 * 1024, 4, 2},  // 15: 30+1 warps, 1 trial per warp, BD 30, BT 640
     {1, 7, 16, 1, 54 * 1024, 4, 2},  // 16: 16+1 warps, 1 trial per warp, BD 16, BT 896
-    // quad patterns: 12 consumer + 12 builder + 1 producer warps, BD 24, BT 896
-    {4, 7, 6, 2, 72 * 1024, 3, 1, 12},  // 17: 3 x 72 KB slots
-    {4, 7, 6, 2, 54 * 1024, 4, 1, 12},  // 18: 4 x 54 KB slots
     // one trial per warp over 17 words (68 samples) per lane: 18 loads per 17
     // words and the table entry and loop overhead spread over twice the words
-    {1, 17, 15, 1, 72 * 1024, 3, 1},   // 19: 15+1 warps, BD 15, BT 2176, 3 x 72 KB (default)
-    {1, 17, 15, 1, 108 * 1024, 2, 1},  // 20: as 19, 2 x 108 KB
-    {1, 19, 11, 1, 72 * 1024, 3, 1},   // 21: 11+1 warps, BD 11, BT 2432
+    {1, 17, 15, 1, 72 * 1024, 3, 1},   // 17: 15+1 warps, BD 15, BT 2176, 3 x 72 KB (default)
+    {1, 17, 15, 1, 108 * 1024, 2, 1},  // 18: as 17, 2 x 108 KB
+    {1, 19, 11, 1, 72 * 1024, 3, 1},   // 19: 11+1 warps, BD 11, BT 2432
 };
 
 namespace {
@@ -148,9 +143,6 @@ __device__ __forceinline__ uint32_t lds32(uint32_t a) {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
-}
-__device__ __forceinline__ void sts64(uint32_t a, uint32_t x, uint32_t y) {
-    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y) : "memory");
 }
 __device__ __forceinline__ uint4 lds128(uint32_t a) {
     uint4 v;
@@ -405,256 +397,6 @@ cudaError_t run_dedisp_rows(const DedispBatch& b, int stage_bytes, int* status,
 }
 
 
-// Quad-pattern kernel (the tile shapes with builder warps; tables in
-// quad_tiling.h).  32*WD*WT consumer warps each own RD trials and NW
-// consecutive words of two 16-bit samples per lane; NBW builder warps form
-// the stage's pattern rows (a lane takes 7 consecutive 4-sample groups of a
-// row: per channel of the quad 8 row words aligned by PRMT, the word sum A and
-// its odd bytes H as in the byte-row kernel, then the group's four 16-bit sums
-// (A - 2^8 H, H) stored as two words); one producer warp stages each stage's
-// channel rows and tables with cp.async.bulk.  Slot b of NB: full[b] (copies
-// landed), built[b] (every builder warp done with the stage's rows), empty[b]
-// (every consumer warp done: the slot may be refilled).  A consumer adds, per
-// trial and quad, NW + 1 row words aligned to the trial's sample parity by one
-// PRMT into 16-bit pair accumulators (at most 64 quads = 256 channels before
-// they are flushed); the flushes add into the int32 output rows in global
-// memory (the first one stores), so the per-sample sums need no registers.
-// Every wait is bounded; no block barrier after set-up.
-template <int RD, int NW, int WD, int WT, int NBW, int NB>
-__global__ void __launch_bounds__(32 * (WD * WT + NBW + 1), 1)
-dedisp_quad_kernel(const __grid_constant__ DedispBatch batch, int slot_bytes, int* status,
-                   uint64_t timeout_ns, uint32_t one) {
-    constexpr int BD = WD * RD;
-    constexpr int NCW = WD * WT;                 // consumer warps
-    constexpr int BT = WT * NW * 64;
-    constexpr int NG = kQuadGroupsPerLane;
-    static_assert(NW % 2 == 1, "an odd word count per lane keeps row loads conflict-free");
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NB * slot_bytes);
-    uint64_t* built = full + NB;
-    uint64_t* empty = built + NB;
-    __shared__ int abort_flag;
-    const uint32_t sbase = smem_u32(smem);
-
-    const int64_t blk = blockIdx.x;
-    int jb = 0;
-    while (jb + 1 < batch.njobs && batch.prefix[jb + 1] <= blk) ++jb;
-    const DedispJob& J = batch.jobs[jb];
-    const int64_t item = blk - batch.prefix[jb];
-    const int64_t per = (int64_t)kTimeGroup * J.ndt;
-    const int64_t grp = item / per;
-    const int64_t rem = item - grp * per;
-    const int64_t gsz = min((int64_t)kTimeGroup, (int64_t)J.ntt - grp * kTimeGroup);
-    const int dt = (int)(rem / gsz);
-    const int tt = (int)(grp * kTimeGroup + rem % gsz);
-    const TileDesc T = J.tiles[dt];
-    const int64_t t0 = (int64_t)tt * BT;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nst = T.nstages;
-
-    if (tid == 0) {
-        for (int b = 0; b < NB; ++b) {
-            mbar_init(&full[b], 1);
-            mbar_init(&built[b], NBW);
-            mbar_init(&empty[b], NCW);
-        }
-        mbar_fence_init();
-        abort_flag = 0;
-    }
-    __syncthreads();
-    volatile int* abort = &abort_flag;
-
-    if (warp == NCW + NBW) {
-        // ------------------------------------------------------- producer
-        int issued = 0;
-        for (int s = 0; s < nst; ++s) {
-            const int b = s % NB;
-            if (s >= NB &&
-                !__all_sync(0xffffffffu, mbar_wait_or_abort(&empty[b], (uint32_t)(s / NB - 1) & 1u,
-                                                            timeout_ns, abort)))
-                break;
-            const StageDesc S = J.stages[T.stage_begin + s];
-            uint8_t* B = smem + b * slot_bytes;
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&full[b], S.tx_bytes);
-                bulk_copy_g2s(B, J.chans + S.chan_begin, S.nchan * (uint32_t)sizeof(ChanDesc),
-                              &full[b]);
-                bulk_copy_g2s(B + S.addr_off, J.addr + S.addr_begin, S.addr_bytes, &full[b]);
-            }
-            __syncwarp();
-            for (uint32_t i = lane; i < S.nchan; i += 32) {
-                const ChanDesc cd = J.chans[S.chan_begin + i];
-                const uint8_t* src = J.xt + (int64_t)cd.c * J.xt_pitch + t0 + cd.goff;
-                bulk_copy_g2s(B + cd.offB, src, 4 * cd.nwords, &full[b]);
-            }
-            issued = s + 1;
-        }
-        if (lane == 0 && *abort) {
-            latch_status(status, HP_ERR_TIMEOUT);
-            for (int x = issued - NB > 0 ? issued - NB : 0; x < issued; ++x)
-                mbar_wait_bounded(&full[x % NB], (uint32_t)(x / NB) & 1u, timeout_ns);
-        }
-        return;
-    }
-
-    if (warp >= NCW) {
-        // ------------------------------------------------------- builders
-        const int bw = warp - NCW;
-        for (int s = 0; s < nst; ++s) {
-            const int b = s % NB;
-            if (!__all_sync(0xffffffffu,
-                            mbar_wait_or_abort(&full[b], (uint32_t)(s / NB) & 1u, timeout_ns, abort)))
-                return;
-            const StageDesc S = J.stages[T.stage_begin + s];
-            const uint32_t B = sbase + (uint32_t)(b * slot_bytes);
-            for (uint32_t p = bw; p < S.npat; p += NBW) {
-                const uint32_t e = B + S.addr_off + p * (uint32_t)sizeof(QPattern);
-                const uint4 h0 = lds128(e), src = lds128(e + 16), sel = lds128(e + 32);
-                const uint32_t dst = B + h0.x, ng = h0.y, nk = h0.z;
-                for (uint32_t g0 = (uint32_t)lane * NG; g0 < ng; g0 += 32 * NG) {
-                    uint32_t A[NG], H[NG];
-#pragma unroll
-                    for (int i = 0; i < NG; ++i) {
-                        A[i] = 0;
-                        H[i] = 0;
-                    }
-                    auto chan = [&](uint32_t s_off, uint32_t s_sel) {
-                        uint32_t w[NG + 1];
-                        const uint32_t a = B + s_off + 4 * g0;
-#pragma unroll
-                        for (int i = 0; i <= NG; ++i) w[i] = lds32(a + 4 * i);
-#pragma unroll
-                        for (int i = 0; i < NG; ++i) {
-                            const uint32_t v = __byte_perm(w[i], w[i + 1], s_sel);
-                            A[i] += v;
-                            H[i] += __byte_perm(v, 0, 0x4341);
-                        }
-                    };
-                    chan(src.x, sel.x);
-                    if (nk > 1) chan(src.y, sel.y);
-                    if (nk > 2) chan(src.z, sel.z);
-                    if (nk > 3) chan(src.w, sel.w);
-#pragma unroll
-                    for (int i = 0; i < NG; ++i) {
-                        if (g0 + i < ng) {
-                            const uint32_t L = A[i] - (H[i] << 8);
-                            sts64(dst + 8 * (g0 + i), __byte_perm(L, H[i], 0x5410),
-                                  __byte_perm(L, H[i], 0x7632));
-                        }
-                    }
-                }
-            }
-            // the pattern rows are generic-proxy writes; the slot's next bulk
-            // copies (async proxy) come after the consumers release it
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&built[b]);
-        }
-        return;
-    }
-
-    // ----------------------------------------------------------- consumers
-    const int wd = warp % WD, wt = warp / WD;
-    uint32_t acc[RD][NW];
-#pragma unroll
-    for (int r = 0; r < RD; ++r)
-#pragma unroll
-        for (int k = 0; k < NW; ++k) acc[r][k] = 0;
-    const uint32_t lane_off = 4u * (uint32_t)(wt * 32 * NW + NW * lane);
-    // first output sample of this lane's words: 2 per word
-    const int64_t tl = t0 + 2 * (int64_t)(wt * 32 * NW + NW * lane);
-    bool first = true;
-    // add the 16-bit pair accumulators into the output rows (the first flush stores)
-    auto flush = [&]() {
-#pragma unroll
-        for (int r = 0; r < RD; ++r) {
-            const int dl = wd * RD + r;
-            if (dl < T.nd) {
-                int32_t* row = J.out + (int64_t)(T.d0 + dl) * J.out_pitch;
-#pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    const int64_t t = tl + 2 * k;
-                    int32_t lo = (int32_t)(acc[r][k] & 0xFFFFu), hi = (int32_t)(acc[r][k] >> 16);
-                    if (t + 1 < J.nout) {
-                        int2* q = reinterpret_cast<int2*>(row + t);
-                        if (!first) {
-                            const int2 o = *q;
-                            lo += o.x;
-                            hi += o.y;
-                        }
-                        *q = make_int2(lo, hi);
-                    } else if (t < J.nout) {
-                        if (!first) lo += row[t];
-                        row[t] = lo;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NW; ++k) acc[r][k] = 0;
-        }
-        first = false;
-    };
-    uint32_t held = 0;
-    for (int s = 0; s < nst; ++s) {
-        const int b = s % NB;
-        const uint32_t ph = (uint32_t)(s / NB) & 1u;
-        if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&full[b], ph, timeout_ns, abort) &&
-                                         mbar_wait_or_abort(&built[b], ph, timeout_ns, abort)))
-            return;
-        const uint32_t B = sbase + (uint32_t)(b * slot_bytes);
-        const StageDesc S = J.stages[T.stage_begin + s];
-        uint32_t tab = B + S.ctab_off + (uint32_t)(wd * RD * 16);
-        const uint32_t tb = B + lane_off;
-        const uint32_t nq = (S.nchan + 3) >> 2;
-        // one quad of trial r: NW + 1 row words from byte address a, the trial's
-        // two samples per word taken by selector sel
-        auto add_q = [&](int r, uint32_t a, uint32_t sel) {
-            uint32_t w[NW + 1];
-#pragma unroll
-            for (int i = 0; i <= NW; ++i) w[i] = lds32(a + 4 * i);
-#pragma unroll
-            for (int i = 0; i < NW; ++i)
-                acc[r][i] = imad_add(acc[r][i], __byte_perm(w[i], w[i + 1], sel), one);
-        };
-        for (uint32_t pr = nq >> 1; pr > 0; --pr, tab += BD * 16) {
-#pragma unroll
-            for (int r = 0; r < RD; ++r) {
-                const uint4 e = lds128(tab + r * 16);
-                add_q(r, tb + e.x, e.z);
-                add_q(r, tb + e.y, e.w);
-            }
-        }
-        if (nq & 1) {   // the odd last quad (its pair entry repeats it)
-#pragma unroll
-            for (int r = 0; r < RD; ++r) {
-                const uint4 e = lds128(tab + r * 16);
-                add_q(r, tb + e.x, e.z);
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[b]);
-        held += S.nchan;
-        const uint32_t next_n = s + 1 < nst ? J.stages[T.stage_begin + s + 1].nchan : 256u;
-        if (held + next_n > 256u) {
-            flush();
-            held = 0;
-        }
-    }
-}
-
-template <int RD, int NW, int WD, int WT, int NBW, int NB>
-cudaError_t run_dedisp_quad(const DedispBatch& b, int slot_bytes, int* status,
-                            uint64_t timeout_ns, cudaStream_t s) {
-    const int64_t total = b.prefix[b.njobs];
-    if (total <= 0) return cudaSuccess;
-    const size_t smem = (size_t)NB * slot_bytes + 3 * NB * 8;
-    auto k = dedisp_quad_kernel<RD, NW, WD, WT, NBW, NB>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)total, 32 * (WD * WT + NBW + 1), smem, s>>>(b, slot_bytes, status, timeout_ns, 1u);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_transpose(const uint8_t* x, int64_t nsamps, int nchans, uint8_t* xt,
@@ -712,11 +454,9 @@ cudaError_t launch_dedisp(int cfg, const DedispBatch& b, int* status, uint64_t t
         case 14: return run_dedisp_rows<1, 7, 24, 1, 4, 2>(b, sb, status, timeout_ns, s);
         case 15: return run_dedisp_rows<1, 5, 30, 1, 4, 2>(b, sb, status, timeout_ns, s);
         case 16: return run_dedisp_rows<1, 7, 16, 1, 4, 2>(b, sb, status, timeout_ns, s);
-        case 17: return run_dedisp_quad<4, 7, 6, 2, 12, 3>(b, sb, status, timeout_ns, s);
-        case 18: return run_dedisp_quad<4, 7, 6, 2, 12, 4>(b, sb, status, timeout_ns, s);
-        case 19: return run_dedisp_rows<1, 17, 15, 1, 3, 1>(b, sb, status, timeout_ns, s);
-        case 20: return run_dedisp_rows<1, 17, 15, 1, 2, 1>(b, sb, status, timeout_ns, s);
-        case 21: return run_dedisp_rows<1, 19, 11, 1, 3, 1>(b, sb, status, timeout_ns, s);
+        case 17: return run_dedisp_rows<1, 17, 15, 1, 3, 1>(b, sb, status, timeout_ns, s);
+        case 18: return run_dedisp_rows<1, 17, 15, 1, 2, 1>(b, sb, status, timeout_ns, s);
+        case 19: return run_dedisp_rows<1, 19, 11, 1, 3, 1>(b, sb, status, timeout_ns, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -36,15 +36,12 @@ struct DedispConfig {
     int stage_bytes;   // shared memory per stage buffer
     int stages;        // stage buffers in the ring
     int unroll;        // channel-pair loop unroll
-    // > 0: the quad-pattern kernel with this many builder warps; its consumer
-    // words hold two 16-bit samples (the byte-row kernel's hold four bytes)
-    int builders;
     int BD() const { return WD * RD; }
-    int BT() const { return WT * NW * (builders ? 64 : 128); }
-    int threads() const { return 32 * (WD * WT + builders + 1); }
+    int BT() const { return WT * NW * 128; }
+    int threads() const { return 32 * (WD * WT + 1); }
 };
-constexpr int kNumDedispConfigs = 22;
-constexpr int kDefaultDedispConfig = 19;
+constexpr int kNumDedispConfigs = 20;
+constexpr int kDefaultDedispConfig = 17;
 // stage 1 of the sub-band variant: its tile shape unless one was set
 constexpr int kDefaultSubbandConfig = 12;
 extern const DedispConfig kDedispConfigs[kNumDedispConfigs];
@@ -74,16 +71,8 @@ struct StageDesc {
     // the block writes its sums to rows seg_row + trial and starts from zero.
     // seg_info: bit 0 = last stage of its segment; bits 1.. = trim: the segment's
     // rows are needed only below nout - trim, so time tiles from there on skip it.
-    // The quad-pattern kernel keeps instead its pattern count and the byte
-    // offset of its consumer table in the slot.
-    union {
-        int32_t seg_row;
-        uint32_t npat;
-    };
-    union {
-        uint32_t seg_info;
-        uint32_t ctab_off;
-    };
+    int32_t seg_row;
+    uint32_t seg_info;
 };
 static_assert(sizeof(StageDesc) == 32, "StageDesc layout");
 

@@ -12,7 +12,6 @@
 #include <vector>
 
 #include "plan_internal.h"
-#include "quad_tiling.h"
 
 using namespace hp;
 
@@ -287,25 +286,6 @@ int build_tiling(hp_plan* p, int cfg, DedispTiling* T) {
                 seg_trim.push_back((uint32_t)(p->sb_maxtop - p->delays[(size_t)d_last * nch + s * S]));
             const int rc = append_tile(delay, nd, nch, seg_begin, seg_row, seg_trim, 0, C, T);
             if (rc) return rc;
-        }
-        T->cfg = cfg;
-        return HP_OK;
-    }
-    if (C.builders > 0) {
-        // quad patterns: the largest tile (up to BD trials) whose every quad fits a slot
-        int d0 = 0;
-        while (d0 < ndm) {
-            int nd = std::min(BD, ndm - d0);
-            const int32_t* base = &p->delays[(size_t)d0 * nch];
-            auto delay = [&](int j, int c) { return base[(size_t)j * nch + c]; };
-            for (;;) {
-                DedispTiling probe;
-                if (append_tile_quad(delay, nd, nch, d0, C, &probe) == HP_OK) break;
-                if (--nd == 0) return HP_ERR_INVALID_ARG;
-            }
-            const int rc = append_tile_quad(delay, nd, nch, d0, C, T);
-            if (rc) return rc;
-            d0 += nd;
         }
         T->cfg = cfg;
         return HP_OK;

@@ -87,7 +87,7 @@ def test_subband_stage1_tile_shape_default():
         p.set_param("subband_chans", 16)
         assert p.get_param("dedisp_config") == 12
         p.set_param("subband_chans", 0)
-        assert p.get_param("dedisp_config") == 19
+        assert p.get_param("dedisp_config") == 17
         p.set_param("dedisp_config", 14)
         p.set_param("subband_chans", 16)
         assert p.get_param("dedisp_config") == 14
@@ -100,7 +100,7 @@ def test_params_roundtrip_and_validation():
     o = w.obs
     with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
         assert p.get_param("w_tol") == w.nw
-        assert p.get_param("dedisp_config") == 19
+        assert p.get_param("dedisp_config") == 17
         for name, val in [("baseline_mode", 1), ("baseline_s", 0.5), ("dm_tol", 3), ("t_gap", -2),
                           ("w_tol", 1), ("raw_capacity", 4096), ("dedisp_config", 3),
                           ("stage_timing", 1), ("timeout_s", 0.25)]:
