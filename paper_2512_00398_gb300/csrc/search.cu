@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kHistThreads, 4) mad_hist_kernel(const int32_t
     constexpr int64_t stride = kHistStep;
     if (vec && yvec && blk0 + kHistBlock <= n) {
         // Whole block, aligned rows: a warp moves the step's 32 pieces of 16
-        // samples (one per lane, 1 KB apart) through shared memory, eight whole
+        // samples (one per lane, a span apart) through shared memory, eight whole
         // 64-byte pieces per load or store instruction; lane l then reads its own
         // piece.  16-byte slot of (piece p, quarter c): 4p + (c ^ ((p >> 1) & 3)),
         // so that both the eight lanes of a cooperative access (pieces p, p + 1,
