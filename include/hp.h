@@ -168,6 +168,20 @@ int hp_plan_destroy(hp_plan* plan);
  * summed blocks are int32).  hp_search, hp_detect and batches follow it;
  * streams refuse it. */
 #define HP_PARAM_DECIMATE 15      /* R: 0 = every start (default) */
+/* Baseline removal fused into dedispersion (Section II-B runs baseline removal
+ * on the dedispersed series; the result is the same either way): with
+ * HP_PARAM_FUSE_LEVELS = 1, the median baseline and at least two remedian
+ * levels, the dedispersion kernel of hp_search, batches and streams also forms
+ * the second remedian level (the median of the five medians of five
+ * consecutive sums) of every 25-sample group inside one of its time tiles from
+ * the sums it holds on chip, and the search forms only the groups straddling a
+ * tile edge or the end of the series from D, so the remedian no longer reads
+ * the whole series.  0 (default): the remedian reads D, as hp_dedisperse and
+ * hp_detect always do.  On the 4096-channel, 2^20-sample, 1500-trial file the
+ * fused kernel instance runs its summation loop 1.4% slower (3.4 ms) and
+ * saves 1.0 ms of search, so the default is off.  The sub-band variant keeps
+ * the unfused remedian. */
+#define HP_PARAM_FUSE_LEVELS 16   /* 1 = second remedian level in the dedispersion epilogue, 0 = off (default) */
 
 #define HP_NUM_DEDISP_CONFIGS 20
 

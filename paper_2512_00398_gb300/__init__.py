@@ -20,7 +20,7 @@ from ._lib import (CAND_DTYPE, EXPORTS, HP_ERR_CAND_OVERFLOW, HP_ERR_CUDA, HP_ER
                    HP_PARAM_STAGE_TIMING, HP_PARAM_T_GAP, HP_PARAM_TIMEOUT_S, HP_PARAM_W_TOL,
                    HP_PARAM_RFI, HP_PARAM_RFI_NB_K, HP_PARAM_RFI_BB_K, HP_STAGE_RFI,
                    HP_PARAM_SUBBAND_CHANS, HP_PARAM_SUBBAND_GROUP, HP_PARAM_WIDTH_SIGMA,
-                   HP_PARAM_DECIMATE,
+                   HP_PARAM_DECIMATE, HP_PARAM_FUSE_LEVELS,
                    HP_STAGE_DEDISP, HP_STAGE_MERGE, HP_STAGE_SEARCH, HP_STAGE_TRANSPOSE, RAW_DTYPE,
                    STAGE_NAMES, HP_BATCH_MAX_FILES, HP_MERGE_STATIC_MAX_RAW, CandBuf, HPError, Peaks,
                    Stats, HP_STREAM_EMPTY, HP_STREAM_MAX_BEAMS, check, lib, status_str)
@@ -32,7 +32,8 @@ _PARAMS = {"baseline_mode": HP_PARAM_BASELINE_MODE, "baseline_s": HP_PARAM_BASEL
            "stage_timing": HP_PARAM_STAGE_TIMING, "timeout_s": HP_PARAM_TIMEOUT_S,
            "rfi": HP_PARAM_RFI, "rfi_nb_k": HP_PARAM_RFI_NB_K, "rfi_bb_k": HP_PARAM_RFI_BB_K,
            "subband_chans": HP_PARAM_SUBBAND_CHANS, "subband_group": HP_PARAM_SUBBAND_GROUP,
-           "width_sigma": HP_PARAM_WIDTH_SIGMA, "decimate": HP_PARAM_DECIMATE}
+           "width_sigma": HP_PARAM_WIDTH_SIGMA, "decimate": HP_PARAM_DECIMATE,
+           "fuse_levels": HP_PARAM_FUSE_LEVELS}
 
 
 def _torch():

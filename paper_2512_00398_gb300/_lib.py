@@ -38,6 +38,7 @@ HP_PARAM_SUBBAND_CHANS = 12
 HP_PARAM_SUBBAND_GROUP = 13
 HP_PARAM_WIDTH_SIGMA = 14
 HP_PARAM_DECIMATE = 15
+HP_PARAM_FUSE_LEVELS = 16
 HP_NUM_DEDISP_CONFIGS = 20
 
 HP_STAGE_TRANSPOSE, HP_STAGE_DEDISP, HP_STAGE_SEARCH, HP_STAGE_MERGE, HP_STAGE_RFI = 0, 1, 2, 3, 4

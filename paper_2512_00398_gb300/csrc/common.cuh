@@ -101,6 +101,26 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst_smem, const void* src_gm
         : "memory");
 }
 
+// Median of five values (the third smallest), by a fixed network of nine
+// compare-exchanges.
+__device__ __forceinline__ int32_t median5(int32_t a, int32_t b, int32_t c, int32_t d, int32_t e) {
+#define HP_CX(x, y) { const int32_t lo_ = min(x, y); y = max(x, y); x = lo_; }
+    HP_CX(a, b); HP_CX(d, e); HP_CX(c, e); HP_CX(c, d); HP_CX(a, d); HP_CX(a, c); HP_CX(b, e);
+    HP_CX(b, d); HP_CX(b, c);
+#undef HP_CX
+    return c;
+}
+
+// Named barrier `id` (1-15; 0 is __syncthreads) over `nthreads` threads (a
+// multiple of 32): wait for all, or arrive without waiting.
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void named_barrier_arrive(int id, int nthreads) {
+    asm volatile("barrier.cta.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Floor division for a positive divisor.
 __device__ __forceinline__ long long floor_div_pos(long long a, long long b) {
     long long q = a / b;

@@ -176,7 +176,7 @@ __device__ __forceinline__ uint32_t imad_add(uint32_t acc, uint32_t x, uint32_t 
 
 // SEG: the tile's stages form segments (sub-band stage 1); the sums are
 // written to rows seg_row + trial after the last stage of each segment.
-template <int RD, int NW, int WD, int WT, int NB, int UNR = 1, bool SEG = false>
+template <int RD, int NW, int WD, int WT, int NB, int UNR = 1, bool SEG = false, bool LV = false>
 __global__ void __launch_bounds__(32 * (WD * WT + 1), 1)
 dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, int* status,
                    uint64_t timeout_ns, uint32_t one) {
@@ -188,6 +188,7 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NB * stage_bytes);
     uint64_t* empty = full + NB;
     __shared__ int abort_flag;
+    __shared__ int done_warps;   // LV: consumer warps that consumed every stage
     const uint32_t sbase = smem_u32(smem);
 
     const int64_t blk = blockIdx.x;
@@ -220,6 +221,7 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
         }
         mbar_fence_init();
         abort_flag = 0;
+        done_warps = 0;
     }
     __syncthreads();
     volatile int* abort = &abort_flag;
@@ -312,8 +314,11 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
         }
         const int b = q % NB;
         if (!__all_sync(0xffffffffu,
-                        mbar_wait_or_abort(&full[b], (uint32_t)(q / NB) & 1u, timeout_ns, abort)))
+                        mbar_wait_or_abort(&full[b], (uint32_t)(q / NB) & 1u, timeout_ns, abort))) {
+            // LV: the epilogue's barrier counts this warp too
+            if constexpr (LV) named_barrier_arrive(1, 32 * NCW);
             return;
+        }
         const uint32_t B = sbase + (uint32_t)(b * stage_bytes);
         const StageDesc S = J.stages[T.stage_begin + s];
         uint32_t tab = B + S.addr_off + (uint32_t)(wd * RD * 16);
@@ -380,7 +385,46 @@ dedisp_rows_kernel(const __grid_constant__ DedispBatch batch, int stage_bytes, i
                     for (int e = 0; e < 4; ++e) sum[r][k][e] = 0;
         }
     }
-    if (!SEG) write_rows(T.d0);
+    if constexpr (!SEG) write_rows(T.d0);
+    if constexpr (LV) {
+        // Second remedian level of the block's sums.  Every consumer warp comes
+        // to this barrier, a warp whose wait gave up by arriving from the stage
+        // loop (each wait is bounded); the finished warps then all read the same
+        // count and go on only if no warp gave up.
+        if (lane == 0) atomicAdd(&done_warps, 1);
+        named_barrier_sync(1, 32 * NCW);
+        if (*reinterpret_cast<volatile int*>(&done_warps) != NCW) return;
+        // The ring is free (every stage consumed, no copy in flight): the sums of
+        // trial dl go to row dl of BT samples.  A lane's NW 16-byte pieces lie
+        // 16 NW bytes apart from the next lane's (NW odd: no bank conflict).
+        int32_t* tile = reinterpret_cast<int32_t*>(smem);
+#pragma unroll
+        for (int r = 0; r < RD; ++r) {
+            int32_t* trow = tile + (wd * RD + r) * BT + wt * 128 * NW;
+#pragma unroll
+            for (int k = 0; k < NW; ++k)
+                *reinterpret_cast<int4*>(trow + 4 * (NW * lane + k)) =
+                    make_int4((int)sum[r][k][0], (int)sum[r][k][1], (int)sum[r][k][2],
+                              (int)sum[r][k][3]);
+        }
+        named_barrier_sync(1, 32 * NCW);
+        // the 25-sample groups [25 g, 25 g + 25) inside [t0, min(t0 + BT, nout)):
+        // median of the five medians of five (threads a group apart read 25 words
+        // apart: no bank conflict)
+        const int64_t te = min(t0 + (int64_t)BT, J.nout);
+        const int64_t g_lo = (t0 + 24) / 25;
+        const int ng = (int)max(te / 25 - g_lo, (int64_t)0);
+        const int items = T.nd * ng;
+        for (int i = tid; i < items; i += 32 * NCW) {
+            const int dl = i / ng, g = i - dl * ng;
+            const int32_t* v = tile + dl * BT + (int)(25 * (g_lo + g) - t0);
+            int32_t m[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                m[j] = median5(v[5 * j], v[5 * j + 1], v[5 * j + 2], v[5 * j + 3], v[5 * j + 4]);
+            J.lv[(int64_t)(T.d0 + dl) * J.lv_pitch + g_lo + g] = median5(m[0], m[1], m[2], m[3], m[4]);
+        }
+    }
 }
 
 template <int RD, int NW, int WD, int WT, int NB, int UNR = 1, bool SEG = false>
@@ -389,7 +433,16 @@ cudaError_t run_dedisp_rows(const DedispBatch& b, int stage_bytes, int* status,
     const int64_t total = b.prefix[b.njobs];
     if (total <= 0) return cudaSuccess;
     const size_t smem = (size_t)NB * stage_bytes + 2 * NB * 8;
-    auto k = dedisp_rows_kernel<RD, NW, WD, WT, NB, UNR, SEG>;
+    // the jobs write the second remedian level (all or none; not the segmented
+    // stage); its epilogue lays the block's sums over the ring
+    const bool lv = b.jobs[0].lv != nullptr;
+    for (int j = 0; j < b.njobs; ++j)
+        if ((b.jobs[j].lv != nullptr) != lv) return cudaErrorInvalidValue;
+    if (lv && (SEG || (size_t)WD * RD * WT * NW * 128 * 4 > (size_t)NB * stage_bytes))
+        return cudaErrorInvalidValue;
+    auto k = dedisp_rows_kernel<RD, NW, WD, WT, NB, UNR, SEG, false>;
+    if constexpr (!SEG)
+        if (lv) k = dedisp_rows_kernel<RD, NW, WD, WT, NB, UNR, false, true>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)total, 32 * (WD * WT + 1), smem, s>>>(b, stage_bytes, status, timeout_ns, 1u);

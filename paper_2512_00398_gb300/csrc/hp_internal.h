@@ -105,6 +105,14 @@ struct DedispJob {
     const StageDesc* stages;
     const ChanDesc* chans;
     const uint32_t* addr;
+    // Median baseline only: the second remedian level of every trial (the median
+    // of the five medians of five consecutive sums of a 25-sample group) for the
+    // groups that lie inside one time tile and below nout, formed from the
+    // block's sums before it leaves, [ndm][lv_pitch]; null: not written (every
+    // job of a launch or none).  The groups that straddle a tile edge or nout are
+    // left to the search.
+    int32_t* lv;
+    int64_t lv_pitch;
 };
 
 // Jobs of one dedispersion launch, passed by value as the kernel parameter.
@@ -207,6 +215,12 @@ struct SearchArgs {
     int baseline_mode;         // 0 median, 1 mean
     int levels;                // remedian levels (median mode)
     int64_t win;               // window in samples (mean mode half width = win/2)
+    // second remedian level of D from the dedispersion (levels >= 2), [ndm][lv2_pitch],
+    // every group of 25 samples inside one of its lv2_bt-sample time tiles; the
+    // groups straddling a tile edge or nout are formed from D here.  Null: the
+    // remedian starts from D.
+    int32_t* lv2;
+    int64_t lv2_pitch, lv2_bt;
     // scratch (device)
     int32_t* lvl_a;            // remedian pass buffers [ndm][lvl_pitch]
     int32_t* lvl_b;

@@ -401,6 +401,11 @@ Layout make_layout(const hp_plan* p, int64_t nsamps, bool with_dedisp) {
         L.dpitch = round_up64(L.nout, 64);
         L.xt = take((size_t)p->nchans * L.xt_pitch);
         L.D = take((size_t)ndm * L.dpitch * 4);
+        if (p->fuse_levels && p->baseline_mode == 0 && p->sb_chans == 0 && L.nout > 0 &&
+            remedian_levels(baseline_window(p)) >= 2) {
+            L.lv2_pitch = round_up64(ceil_div(L.nout, 25), 4);
+            L.lv2 = take((size_t)ndm * L.lv2_pitch * 4);
+        }
         if (p->sb_chans > 0 && L.nout > 0) {
             // partial sums B of whole chunks of BD groups: nsub * BD rows per chunk
             const int64_t BD = kDedispConfigs[p->dedisp_cfg].BD();
@@ -649,7 +654,27 @@ DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_
     J.stages = p->d_stages;
     J.chans = p->d_chans;
     J.addr = p->d_addr;
+    J.lv = nullptr;
+    J.lv_pitch = 0;
     return J;
+}
+
+// The dedispersion of the plan's own series also writes the second remedian
+// level (median baseline with at least two levels, direct dedispersion: the
+// layout holds the buffer only then), and the search starts from it.
+void fuse_levels(DedispJob& J, const Layout& L, uint8_t* ws) {
+    if (L.lv2_pitch > 0) {
+        J.lv = (int32_t*)(ws + L.lv2);
+        J.lv_pitch = L.lv2_pitch;
+    }
+}
+
+void fuse_levels(SearchArgs& a, const Layout& L, uint8_t* ws, int cfg) {
+    if (L.lv2_pitch > 0) {
+        a.lv2 = (int32_t*)(ws + L.lv2);
+        a.lv2_pitch = L.lv2_pitch;
+        a.lv2_bt = kDedispConfigs[cfg].BT();
+    }
 }
 
 // Stages 1 and 2 of the sub-band variant on the transposed input: per chunk
@@ -710,7 +735,7 @@ int run_subband(hp_plan* p, const Layout& L, uint8_t* ws, int32_t* out, int64_t 
 // Transpose, optional RFI mitigation, dedispersion (direct or sub-band) of one
 // input into out[ndm][out_pitch].
 int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, const Layout& L, uint8_t* ws,
-               int32_t* out, int64_t out_pitch, cudaStream_t s, bool with_rfi) {
+               int32_t* out, int64_t out_pitch, cudaStream_t s, bool with_rfi, bool own_series) {
     uint8_t* xt = ws + L.xt;
     const int64_t xt_pitch = L.xt_pitch;
     const int64_t nout = nsamps - p->maxd;
@@ -732,6 +757,7 @@ int run_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, const Layout& L, u
     B.njobs = 1;
     if (!reach_ok(p, nout, xt_pitch)) return HP_ERR_INVALID_ARG;
     B.jobs[0] = make_job(p, xt, xt_pitch, out, out_pitch, nout);
+    if (own_series) fuse_levels(B.jobs[0], L, ws);
     B.prefix[0] = 0;
     B.prefix[1] = (int64_t)B.jobs[0].ntt * B.jobs[0].ndt;
     ti = stage_begin(p, HP_STAGE_DEDISP, s);
@@ -763,6 +789,9 @@ SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int3
     a.baseline_mode = p->baseline_mode;
     a.win = baseline_window(p);
     a.levels = remedian_levels(a.win);
+    a.lv2 = nullptr;
+    a.lv2_pitch = 0;
+    a.lv2_bt = 0;
     a.lvl_a = (int32_t*)(ws + L.lvl_a);
     a.lvl_b = (int32_t*)(ws + L.lvl_b);
     a.lvl_pitch_a = L.lvl_pitch_a;
@@ -928,10 +957,10 @@ int time_dedisp(hp_plan* p, const uint8_t* fb, int64_t nsamps, cudaStream_t s, i
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return HP_ERR_CUDA; }
     const bool timing = p->timing;
     p->timing = false;
-    rc = run_dedisp(p, fb, nsamps, L, ws, (int32_t*)(ws + L.D), L.dpitch, s, false);
+    rc = run_dedisp(p, fb, nsamps, L, ws, (int32_t*)(ws + L.D), L.dpitch, s, false, false);
     if (!rc) rc = check_cuda(cudaEventRecord(e0, s));
     for (int r = 0; r < reps && !rc; ++r)
-        rc = run_dedisp(p, fb, nsamps, L, ws, (int32_t*)(ws + L.D), L.dpitch, s, false);
+        rc = run_dedisp(p, fb, nsamps, L, ws, (int32_t*)(ws + L.D), L.dpitch, s, false, false);
     if (!rc) rc = check_cuda(cudaEventRecord(e1, s));
     if (!rc) rc = check_cuda(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -1042,6 +1071,7 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
             std::memset(&db, 0, sizeof(db));
             db.njobs = 1;
             db.jobs[0] = make_job(p, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, L.nout);
+            fuse_levels(db.jobs[0], L, ws);
             db.prefix[1] = (int64_t)db.jobs[0].ntt * db.jobs[0].ndt;
             rc = check_cuda(launch_dedisp(b->cfg, db, p->status, p->timeout_ns, s));
             if (rc) return rc;
@@ -1056,6 +1086,7 @@ int batch_enqueue(hp_batch* b, const uint8_t* const* fbs, const int64_t* nsamps,
         int64_t* raw_count = (int64_t*)(ws + L.raw_count);
         SearchArgs a = make_search_args(p, L, ws, (int32_t*)(ws + L.D), L.dpitch, L.nout, raw,
                                         p->raw_capacity, raw_count);
+        if (p->sb_chans <= 0) fuse_levels(a, L, ws, b->cfg);
         rc = check_cuda(launch_search(a, si, &k));
         if (rc) return rc;
         MergeArgs m = make_merge_args(p, L, ws, raw, raw_count, p->raw_capacity, a.sigma, &outs[i]);
@@ -1250,6 +1281,10 @@ int hp_plan_set_param(hp_plan* p, int param, double v) {
                 p->dedisp_cfg = p->sb_chans > 0 ? kDefaultSubbandConfig : kDefaultDedispConfig;
             apply_subband(p);
             return HP_OK;
+        case HP_PARAM_FUSE_LEVELS:
+            if (v != 0.0 && v != 1.0) return HP_ERR_INVALID_ARG;
+            p->fuse_levels = v == 1.0;
+            return HP_OK;
         case HP_PARAM_SUBBAND_GROUP:
             if (v < 1 || v > p->ndm() || v != std::floor(v)) return HP_ERR_INVALID_ARG;
             p->sb_group = (int)v;
@@ -1279,6 +1314,7 @@ int hp_plan_get_param(const hp_plan* p, int param, double* v) {
         case HP_PARAM_WIDTH_SIGMA: *v = p->width_sigma ? 1.0 : 0.0; return HP_OK;
         case HP_PARAM_DECIMATE: *v = p->decimate; return HP_OK;
         case HP_PARAM_SUBBAND_GROUP: *v = p->sb_group; return HP_OK;
+        case HP_PARAM_FUSE_LEVELS: *v = p->fuse_levels ? 1.0 : 0.0; return HP_OK;
         default: return HP_ERR_INVALID_ARG;
     }
 }
@@ -1375,7 +1411,7 @@ int hp_dedisperse(hp_plan* p, const uint8_t* fb, int64_t nsamps, int32_t* out, i
     uint8_t* ws = nullptr;
     rc = ensure_workspace(p, L.total, &ws);
     if (rc) return rc;
-    return run_dedisp(p, fb, nsamps, L, ws, out, pitch, (cudaStream_t)stream, true);
+    return run_dedisp(p, fb, nsamps, L, ws, out, pitch, (cudaStream_t)stream, true, false);
 }
 
 int hp_detect(hp_plan* p, const int32_t* series, int64_t nout, int64_t pitch, void* stream,
@@ -1438,11 +1474,12 @@ int hp_search(hp_plan* p, const uint8_t* fb, int64_t nsamps, void* stream, hp_ca
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t* D = (int32_t*)(ws + L.D);
-    rc = run_dedisp(p, fb, nsamps, L, ws, D, L.dpitch, s, true);
+    rc = run_dedisp(p, fb, nsamps, L, ws, D, L.dpitch, s, true, true);
     if (rc) return rc;
     hp_raw_cand* raw = (hp_raw_cand*)(ws + L.raw);
     int64_t* raw_count = (int64_t*)(ws + L.raw_count);
     SearchArgs a = make_search_args(p, L, ws, D, L.dpitch, L.nout, raw, p->raw_capacity, raw_count);
+    fuse_levels(a, L, ws, p->dedisp_cfg);
     int ti = stage_begin(p, HP_STAGE_SEARCH, s);
     rc = check_cuda(launch_search(a, s, &p->launches));
     stage_end(p, HP_STAGE_SEARCH, ti, s);

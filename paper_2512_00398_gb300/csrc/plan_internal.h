@@ -37,6 +37,10 @@ struct Layout {
     size_t sb = 0;             // sub-band partial sums (sub-band variant)
     int64_t sb_pitch = 0, sb_len = 0;
     int sb_chunks = 0;         // DM-tile chunks whose partial sums fit `sb` at once
+    // second remedian level of D, written by the dedispersion (median baseline,
+    // at least two levels, direct dedispersion): [ndm][lv2_pitch]
+    size_t lv2 = 0;
+    int64_t lv2_pitch = 0;
     size_t y = 0;              // baseline-subtracted series (unless it overwrites D)
     int64_t ypitch = 0;
     bool y_in_D = false;
@@ -58,6 +62,7 @@ struct hp_plan {
     int64_t t_gap = 0;
     int w_tol = 0;
     int64_t raw_capacity = (int64_t)1 << 22;
+    bool fuse_levels = false;          // second remedian level in the dedispersion epilogue
     int dedisp_cfg = hp::kDefaultDedispConfig;
     bool dedisp_cfg_set = false;       // a tile shape was set (or autotuned) by the caller
     uint64_t timeout_ns = 1000000000ull;
@@ -135,6 +140,11 @@ DedispJob make_job(const hp_plan* p, const uint8_t* xt, int64_t xt_pitch, int32_
 // Stages 1 and 2 of the sub-band variant on the transposed input at ws + L.xt.
 int run_subband(hp_plan* p, const Layout& L, uint8_t* ws, int32_t* out, int64_t out_pitch,
                 cudaStream_t s);
+// The dedispersion of the plan's own series also writes the second remedian
+// level, and the search of that series (dedispersed with tile shape cfg)
+// starts from it; no-ops unless the layout holds the level buffer.
+void fuse_levels(DedispJob& J, const Layout& L, uint8_t* ws);
+void fuse_levels(SearchArgs& a, const Layout& L, uint8_t* ws, int cfg);
 SearchArgs make_search_args(hp_plan* p, const Layout& L, uint8_t* ws, const int32_t* D,
                             int64_t pitch, int64_t nout, hp_raw_cand* raw, int64_t raw_cap,
                             int64_t* raw_count);

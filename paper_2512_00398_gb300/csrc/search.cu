@@ -29,13 +29,7 @@ constexpr int64_t kNever = LLONG_MAX;
 
 // ------------------------------------------------------------- remedian
 __device__ __forceinline__ int32_t lower_median_small(const int32_t* v, int r) {
-    if (r >= 5) {
-        int32_t a = v[0], b = v[1], c = v[2], d = v[3], e = v[4];
-#define CS(x, y) { int32_t lo_ = min(x, y); int32_t hi_ = max(x, y); x = lo_; y = hi_; }
-        CS(a, b); CS(d, e); CS(c, e); CS(c, d); CS(a, d); CS(a, c); CS(b, e); CS(b, d); CS(b, c);
-#undef CS
-        return c;
-    }
+    if (r >= 5) return median5(v[0], v[1], v[2], v[3], v[4]);
     if (r == 4) {
         const int32_t p = min(v[0], v[1]), P = max(v[0], v[1]);
         const int32_t q = min(v[2], v[3]), Q = max(v[2], v[3]);
@@ -44,6 +38,40 @@ __device__ __forceinline__ int32_t lower_median_small(const int32_t* v, int r) {
     if (r == 3) return max(min(v[0], v[1]), min(max(v[0], v[1]), v[2]));
     if (r == 2) return min(v[0], v[1]);
     return v[0];
+}
+
+// Second-level remedian values the dedispersion could not form: the group of
+// 25 samples straddling each edge k bt of its time tiles (0 < k < ntt, unless
+// the edge is a multiple of 25) and a last partial group (lower medians of a
+// short group, as in the passes below).  Thread k of row `trial`, k in 1..ntt.
+__global__ void __launch_bounds__(128) level2_fixup_kernel(const int32_t* __restrict__ D,
+                                                           int64_t pitch, int64_t n, int64_t bt,
+                                                           int32_t* __restrict__ lv,
+                                                           int64_t lv_pitch) {
+    const int trial = blockIdx.y;
+    const int64_t ntt = (n + bt - 1) / bt;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 1 || k > ntt) return;
+    int64_t g;
+    if (k < ntt) {
+        const int64_t e = k * bt;   // e < n
+        if (e % 25 == 0) return;
+        g = e / 25;
+    } else {
+        g = (n - 1) / 25;
+        if (25 * g + 25 <= n) return;
+    }
+    const int32_t* row = D + (int64_t)trial * pitch + 25 * g;
+    const int cnt = (int)min((int64_t)25, n - 25 * g);
+    const int nm = (cnt + 4) / 5;
+    int32_t m[5];
+    for (int j = 0; j < nm; ++j) {
+        int32_t v[5];
+        const int r = min(5, cnt - 5 * j);
+        for (int i = 0; i < r; ++i) v[i] = row[5 * j + i];
+        m[j] = lower_median_small(v, r);
+    }
+    lv[(int64_t)trial * lv_pitch + g] = lower_median_small(m, nm);
 }
 
 __constant__ int64_t kPow5[14] = {1, 5, 25, 125, 625, 3125, 15625, 78125, 390625, 1953125,
@@ -137,10 +165,10 @@ struct MedianWalkerT {
         int64_t nx;
         PI = (I)P;
         if (M == 1 || t <= half) {
-            base = m[0]; q = 0; r = 0; interior = false;
+            base = m[0]; q = 0; r = 0; dq = 0; dr = 0; interior = false;
             nx = (M == 1) ? LLONG_MAX : half + 1;
         } else if (t >= c_last) {
-            base = m[M - 1]; q = 0; r = 0; interior = false;
+            base = m[M - 1]; q = 0; r = 0; dq = 0; dr = 0; interior = false;
             nx = LLONG_MAX;
         } else {
             const int64_t j = (t - half) / P;
@@ -168,6 +196,24 @@ struct MedianWalkerT {
             r += dr;
             if (r >= PI) { r -= PI; ++q; }
         }
+    }
+    // y = v - b over the next N samples when no new interval starts among them
+    // (left > N): the plain update, which the flat parts (dq = dr = 0) share;
+    // f(y) for each
+    template <int N, class F>
+    __device__ __forceinline__ void subtract_run(int32_t (&v)[N], F&& f) {
+        I q_ = q, r_ = r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            v[i] = (int32_t)((int64_t)v[i] - (int64_t)(base + q_));
+            f(v[i]);
+            q_ += dq;
+            r_ += dr;
+            if (r_ >= PI) { r_ -= PI; ++q_; }
+        }
+        q = q_;
+        r = r_;
+        left -= N;
     }
 };
 
@@ -371,15 +417,24 @@ __global__ void __launch_bounds__(kHistThreads, 4) mad_hist_kernel(const int32_t
                 const int4 x = T[slot(lane, c)];
                 v[4 * c] = x.x; v[4 * c + 1] = x.y; v[4 * c + 2] = x.z; v[4 * c + 3] = x.w;
             }
-#pragma unroll
-            for (int q = 0; q < kHistStep; ++q) {
-                const int32_t y = (int32_t)((int64_t)v[q] - w.value());
-                v[q] = y;
+            auto count = [&](int32_t y) {
                 const uint32_t m = y < 0 ? 0u - (uint32_t)y : (uint32_t)y;
                 atomicAdd(&h[m < (uint32_t)kHistFine ? (int)m
                                                      : kHistFine + (int)min(m >> 12, (uint32_t)(kHistFine - 1))],
                           1u);
-                w.step();
+            };
+            bool fast = false;
+            if constexpr (MODE != 1) fast = w.left > kHistStep;
+            if (fast) {
+                if constexpr (MODE != 1) w.subtract_run(v, count);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kHistStep; ++q) {
+                    const int32_t y = (int32_t)((int64_t)v[q] - w.value());
+                    v[q] = y;
+                    count(y);
+                    w.step();
+                }
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -1786,9 +1841,23 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t s, int64_t* nlaunch)
         } else {
             const int32_t* in = a.D;
             int64_t in_pitch = a.pitch, n_in = n;
+            int left = L;
+            if (a.lv2 != nullptr && L >= 2) {
+                // the dedispersion formed the second level of every group inside
+                // one of its time tiles; the straddling groups come from D
+                const int64_t ntt = ceil_div(n, a.lv2_bt);
+                ++*nlaunch;
+                level2_fixup_kernel<<<dim3((unsigned)ceil_div(ntt + 1, 128), ndm), 128, 0, s>>>(
+                    a.D, a.pitch, n, a.lv2_bt, a.lv2, a.lv2_pitch);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                in = a.lv2;
+                in_pitch = a.lv2_pitch;
+                n_in = ceil_div(n, 25);
+                left = L - 2;
+            }
             int32_t* bufs[2] = {a.lvl_a, a.lvl_b};
             const int64_t pitches[2] = {a.lvl_pitch_a, a.lvl_pitch_b};
-            int left = L, which = 0;
+            int which = 0;
             while (left > 0) {
                 const int q = left < 5 ? left : 5;
                 int64_t chunk = 1;

@@ -282,6 +282,9 @@ int enqueue_step(hp_stream* s, Step* st) {
         const int64_t nsamps = it.E - it.B0;
         Ls.push_back(make_layout(p, nsamps, true));
         const Layout& L = Ls.back();
+        // the plan's parameters set the layout; one changed since the stream
+        // opened may need more than the step slot holds
+        if (L.total > s->ws_bytes) return HP_ERR_INVALID_ARG;
         uint8_t* ws = s->ws[j];
         TransposeJob J = make_transpose_job(s->slots[it.slot].ring, nsamps, s->nch, ws + L.xt,
                                             L.xt_pitch);
@@ -293,6 +296,7 @@ int enqueue_step(hp_stream* s, Step* st) {
         if (p->sb_chans <= 0) {   // the sub-band variant runs its own two stages per gulp
             if (!reach_ok(p, L.nout, L.xt_pitch)) return HP_ERR_INVALID_ARG;
             db.jobs[j] = make_job(p, ws + L.xt, L.xt_pitch, (int32_t*)(ws + L.D), L.dpitch, L.nout);
+            fuse_levels(db.jobs[j], L, ws);
             db.prefix[j + 1] = db.prefix[j] + (int64_t)db.jobs[j].ntt * db.jobs[j].ndt;
         }
         work.push_back(&it);
@@ -327,6 +331,7 @@ int enqueue_step(hp_stream* s, Step* st) {
             int64_t* raw_count = (int64_t*)(ws + L.raw_count);
             SearchArgs a = make_search_args(p, L, ws, (int32_t*)(ws + L.D), L.dpitch, L.nout, raw,
                                             p->raw_capacity, raw_count);
+            if (p->sb_chans <= 0) fuse_levels(a, L, ws, p->dedisp_cfg);
             a.nwin = it.nwin;
             a.carry_in = it.carry_valid ? B.carry[it.cin] : nullptr;
             a.carry_out = B.carry[it.cin ^ 1];
