@@ -39,17 +39,15 @@ METRIC = "DM-trial·samples/s"
 # scaled by the number of time tiles to the full nout of 955 060.  Keyed by the kernel
 # source it was measured on; a changed kernel, another workload or another
 # configuration reports null until it is captured again.
-DEDISP_TRAFFIC = {"source_sha256_16": "0954eac5d78321ca", "bytes": (6.091e9 + 1.008e9) * 955060 / 168628,
+DEDISP_TRAFFIC = {"source_sha256_16": "0e82e2697ab3fb83", "bytes": (6.095e9 + 1.010e9) * 955060 / 168628,
                   "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 17}
 # The same for the two stages of the sub-band variant (64-channel sub-bands, groups
 # of 8 trials): DRAM bytes of one step, captured on the 2^18-sample case
 # (profiles/subband_fast_4096ch.md).  Stage 1's traffic grows with its byte-adds
 # (scaled by 7.445e11 / 1.389e11 to the full file, within 0.5% of an earlier full-size
 # capture); stage 2's partial-sum rows do not scale with the file length, so it stays null.
-# (Keyed by the current sources: the segmented stage-1 kernel is unchanged since the capture;
-# only the transpose and the removed quad-pattern kernel changed in the same file.)
-SUBBAND_TRAFFIC = {"source_sha256_16": "0954eac5d78321ca+6752b94441917dc0",
-                   "stage1": (6.041e9 + 8.657e9) * 7.445e11 / 1.389e11, "stage2": None,
+SUBBAND_TRAFFIC = {"source_sha256_16": "0e82e2697ab3fb83+6752b94441917dc0",
+                   "stage1": (6.036e9 + 8.660e9) * 7.445e11 / 1.389e11, "stage2": None,
                    "ndm": 1500, "nchans": 4096, "nsamps": 1 << 20, "config": 12, "S": 64, "G": 8}
 
 
@@ -63,6 +61,8 @@ def parse():
     ap.add_argument("--nsamps", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="skip the search with the remedian levels fused into dedispersion")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 16-file batched-vs-plain measurement")
     ap.add_argument("--batch-files", type=int, default=16)
@@ -337,6 +337,32 @@ def run_ours(args):
     rstats = hp.hp_plan_stats(plan, reset=True)
     rfi_ms = rstats["stage_ms"]["rfi"] / max(1, rstats["stage_calls"]["rfi"])
     plan.set_param("rfi", 0)
+    # the same search with the second remedian level formed in the dedispersion
+    # epilogue (HP_PARAM_FUSE_LEVELS = 1, not the default): stage times and step
+    # time over `steps` searches, candidates identical to the default path's
+    fused = None
+    if not args.no_fused:
+        plan.set_param("fuse_levels", 1)
+        plan.bind_workspace(o.nsamps)
+        for _ in range(2):
+            hp.hp_search(plan, fb, stream, out=out)
+        hp.hp_plan_stats(plan, reset=True)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            hp.hp_search(plan, fb, stream, out=out)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fst_code = hp.hp_plan_sync_status(plan, stream)
+        if fst_code != hp.HP_OK:
+            raise hp.HPError(fst_code, "fused search")
+        fst = hp.hp_plan_stats(plan, reset=True)
+        fused = {"ms_per_step": f0.elapsed_time(f1) / args.steps,
+                 "stages_ms": {k: v / max(1, fst["stage_calls"][k])
+                               for k, v in fst["stage_ms"].items() if v},
+                 "identical_candidates": bool(np.array_equal(hp.cands_to_numpy(*out), cands))}
+        plan.set_param("fuse_levels", 0)
     plan.set_param("stage_timing", 0)
 
     # end to end through the public call: every step copies its 4.3 GB input from
@@ -414,6 +440,13 @@ def run_ours(args):
             "gpu_launches": stats["kernel_launches"],
             "rfi_stage_ms": rfi_ms,
         }
+        if fused is not None:
+            fused["unfused_ms_per_step"] = dev_ms
+            fused["unfused_stages_ms"] = line["stages_ms"]
+            fused["note"] = ("HP_PARAM_FUSE_LEVELS = 1: the dedispersion epilogue forms the "
+                             "second remedian level, the remedian no longer reads D; off by "
+                             "default (the fused kernel instance's summation loop is slower)")
+            line["fused_levels"] = fused
         peaks = hp.hp_measure_peaks()
         sm_mhz = clocks["sm_mhz"] or 0.0
         # ALU roofline: 16-bit x 2 SWAR lanes give two byte-adds per 32-bit lane
