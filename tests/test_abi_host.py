@@ -128,6 +128,41 @@ def test_workspace_sizes():
         assert e.value.code == hp.HP_ERR_NSAMPS_TOO_SHORT
 
 
+def test_fuse_levels_param_and_workspace():
+    """HP_PARAM_FUSE_LEVELS: off by default, 0 or 1 only; on, the workspace holds
+    the second remedian level [ndm][round4(ceil(nout / 25))] int32 (256-byte
+    aligned) for the median baseline with at least two levels and direct
+    dedispersion, and nothing more otherwise."""
+    w = workloads.fast(nsamps=1 << 20)
+    o = w.obs
+    with hp.Plan(o.nchans, o.f_top, o.chan_bw, o.tsamp, w.dm_list, w.widths, 6.0) as p:
+        assert p.get_param("fuse_levels") == 0
+        for bad in (-1, 0.5, 2):
+            with pytest.raises(hp.HPError):
+                p.set_param("fuse_levels", bad)
+        nout = p.nout(1 << 20)
+        plain = p.workspace_bytes(1 << 20)
+        p.set_param("fuse_levels", 1)
+        lv2 = w.ndm * ((-(-nout // 25) + 3) // 4 * 4) * 4
+        assert p.workspace_bytes(1 << 20) - plain == (lv2 + 255) // 256 * 256
+        p.set_param("baseline_mode", 1)                     # moving mean: no remedian
+        mean = p.workspace_bytes(1 << 20)
+        p.set_param("fuse_levels", 0)
+        assert p.workspace_bytes(1 << 20) == mean
+        p.set_param("fuse_levels", 1)
+        p.set_param("baseline_mode", 0)
+        p.set_param("baseline_s", 0.0005)                  # one level (10 samples)
+        one = p.workspace_bytes(1 << 20)
+        p.set_param("fuse_levels", 0)
+        assert p.workspace_bytes(1 << 20) == one
+        p.set_param("fuse_levels", 1)
+        p.set_param("baseline_s", 2.0)
+        p.set_param("subband_chans", 64)                   # the sub-band variant keeps D's remedian
+        sb = p.workspace_bytes(1 << 20)
+        p.set_param("fuse_levels", 0)
+        assert p.workspace_bytes(1 << 20) == sb
+
+
 @pytest.mark.parametrize("kw", [dict(nbeams=0), dict(nbeams=hp.HP_STREAM_MAX_BEAMS + 1),
                                 dict(gulp=32), dict(max_batch=-1), dict(max_batch=33),
                                 dict(hbm_budget=-5), dict(cand_capacity=0),

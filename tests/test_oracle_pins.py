@@ -175,6 +175,24 @@ def test_baseline_median_bruteforce(n, L):
     assert (oracle.remedian(D, L) == np.array(_remedian_brute(D.tolist(), L))).all()
 
 
+@pytest.mark.parametrize("n", [1, 24, 25, 26, 3124, 3125, 3126, 15625 + 17, 40000])
+def test_remedian_levels_compose(n):
+    """The remedian's levels compose: L levels over D equal L - 2 levels over the
+    second-level values (medians of five medians of five, over groups of 25
+    aligned samples, the trailing partial groups by their lower medians); the
+    fused search forms those values first and runs the remaining levels on them."""
+    rng = np.random.default_rng(n)
+    D = rng.integers(0, 1 << 20, size=n).astype(np.int32)
+    lv2 = oracle.remedian(D, 2)
+    assert lv2.size == -(-n // 25)
+    for g in (0, lv2.size - 1):
+        grp = D[25 * g:25 * g + 25].tolist()
+        meds = [sorted(grp[i:i + 5])[(len(grp[i:i + 5]) - 1) // 2] for i in range(0, len(grp), 5)]
+        assert lv2[g] == sorted(meds)[(len(meds) - 1) // 2]
+    for L in range(2, 7):
+        assert np.array_equal(oracle.remedian(D, L), oracle.remedian(lv2.astype(np.int32), L - 2)), L
+
+
 def test_baseline_median_monotone_and_ramp():
     L, P = 3, 125
     n = 8 * P
